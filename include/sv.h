@@ -1,0 +1,192 @@
+/*
+ * libsv -- C-ABI of the GB300 statevector engine.
+ *
+ * The library applies a circuit's gate list to a 2^n complex statevector held
+ * in the GPU's HBM: the full-circuit execution path the paper compares
+ * (Sec. III-B, Listing 3: circuit in, full probability vector out), which also
+ * simulates every cut-subcircuit instance of the CutQC Evaluator (Sec. IV-A,
+ * "Evaluator"; Fig. 1).  Every step of the path runs in the library's own
+ * sm_103a kernels; there is no CPU fallback.
+ *
+ * Conventions (all entry points)
+ *   - Amplitude i of an n-qubit state is stored at element i; index bit q is
+ *     qubit q (little-endian, as the Statevector.probabilities call of
+ *     Listings 2 and 3).  Amplitudes are interleaved (re, im):
+ *     SV_C64 = 2 x float32 (8 bytes), SV_C128 = 2 x float64 (16 bytes), so a
+ *     state takes 2^n * 8 or 2^n * 16 bytes (Table III lists the latter).
+ *   - Every call returns SV_OK (0) or a negative sv_status; no C++ exception
+ *     crosses this boundary.  sv_status_str() maps a code to a static string.
+ *   - Pointers named *_host are host memory; pointers with an *_is_device flag
+ *     may be either.  The caller owns every buffer it passes and must keep it
+ *     valid for the duration of the call only: calls are synchronous unless
+ *     stated otherwise.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef LIBSV_SV_H
+#define LIBSV_SV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SV_OK = 0,
+    SV_ERR_ARG = -1,      /* null pointer, bad enum value, non-finite angle  */
+    SV_ERR_QUBIT = -2,    /* qubit index out of range or repeated operands   */
+    SV_ERR_OOM = -3,      /* device allocation failed / does not fit in HBM  */
+    SV_ERR_SIZE = -4,     /* output length or byte count does not match 2^n  */
+    SV_ERR_CUDA = -5,     /* a CUDA runtime call failed                      */
+    SV_ERR_TIMEOUT = -6,  /* a bounded device-side wait ran out              */
+    SV_ERR_STATE = -7     /* handle used after a failure left it undefined   */
+} sv_status;
+
+typedef enum { SV_C64 = 0, SV_C128 = 1 } sv_dtype;
+
+/* Gate set of the engine.  Matrices follow Qiskit's conventions (the paper
+ * runs Qiskit 1.0.2 and Aer 0.14, Sec. V-A), global phases included:
+ *   H = [[1,1],[1,-1]]/sqrt2   X   Y = [[0,-i],[i,0]]   Z = diag(1,-1)
+ *   S = diag(1,i)   T = diag(1,e^{i pi/4})
+ *   RX(t) = [[c,-is],[-is,c]]   RY(t) = [[c,-s],[s,c]]   RZ(t) = diag(e^{-it/2}, e^{it/2})
+ *   U3(t,p,l) = [[c, -e^{il} s], [e^{ip} s, e^{i(p+l)} c]]     (c = cos t/2, s = sin t/2)
+ * Two-qubit gates act on the local index b(q0) + 2 b(q1):
+ *   CX (q0 = control, q1 = target)   CZ = diag(1,1,1,-1)
+ *   RZZ(t) = diag(e^{-it/2}, e^{it/2}, e^{it/2}, e^{-it/2})   SWAP              */
+typedef enum {
+    SV_H = 0, SV_X, SV_Y, SV_Z, SV_S, SV_T, SV_RX, SV_RY, SV_RZ, SV_U3,
+    SV_CX, SV_CZ, SV_RZZ, SV_SWAP, SV_NUM_OPS
+} sv_op;
+
+/* One gate: q1 = -1 for one-qubit gates; theta/phi/lambda unused by fixed
+ * gates.  40 bytes: int32 x 3, 4 bytes padding, float64 x 3. */
+typedef struct {
+    int32_t op, q0, q1;
+    double theta, phi, lambda;
+} sv_gate;
+
+/* Arithmetic used for complex128 states.
+ *   SV_ARITH_NATIVE: IEEE float64 multiply-adds on the FP64 units.
+ *   SV_ARITH_DF64:   float64 storage, gate arithmetic in double-float pairs on
+ *                    the FP32 units (error-free TwoProd / TwoSum transforms,
+ *                    Dekker 1971; Joldes, Muller, Popescu 2017), about 47
+ *                    significant bits per operation.
+ * complex64 states always compute in float32. */
+typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_NATIVE = 1, SV_ARITH_DF64 = 2 } sv_arith;
+
+/* Run options; a null pointer or 0 fields mean "auto".
+ *   max_fuse_k:   largest fused block, 1..5 qubits; 1 = no fusion (each gate
+ *                 is applied on its own).
+ *   tile_qubits:  qubits per shared-memory tile (cache blocking, the
+ *                 single-GPU counterpart of the chunk size nc, Sec. III-B).
+ *   arith:        sv_arith for complex128 states.
+ *   debug_checks: nonzero = check the plan's invariants before launching.   */
+typedef struct {
+    int32_t max_fuse_k;
+    int32_t tile_qubits;
+    int32_t arith;
+    int32_t debug_checks;
+} sv_run_opts;
+
+typedef struct sv_state sv_state;
+
+/* Bytes of a state: 2^n * 8 (SV_C64) or 2^n * 16 (SV_C128); 0 if n is not in
+ * 1..34 or dt is not a sv_dtype.  Host-only; Table III's sizes. */
+size_t sv_state_bytes(int n_qubits, int dt);
+
+/* Creates an n-qubit state (1 <= n <= 34) in a device buffer the library
+ * allocates and owns, initialised to |0...0>, on the current CUDA device and
+ * a stream the library creates.  SV_ERR_OOM if it does not fit. */
+int sv_create(int n_qubits, int dt, sv_state** out);
+
+/* Wraps a caller-owned device buffer (for example a torch tensor) of
+ * exactly sv_state_bytes(n, dt) bytes, 16-byte aligned, as a state.  The
+ * buffer's contents are taken as the state (no initialisation).  Work is
+ * issued on cuda_stream (a cudaStream_t; NULL = the legacy default stream).
+ * The caller keeps the buffer alive until sv_destroy. */
+int sv_create_on(void* dev_ptr, size_t bytes, int n_qubits, int dt,
+                 void* cuda_stream, sv_state** out);
+
+/* Frees the handle and, unless created by sv_create_on, its buffer. */
+void sv_destroy(sv_state* s);
+
+int sv_num_qubits(const sv_state* s);
+int sv_dtype_of(const sv_state* s);
+/* Device pointer of the amplitudes (for zero-copy interop). */
+void* sv_device_ptr(const sv_state* s);
+
+/* Sets the state to the basis state |basis_index> (< 2^n). */
+int sv_reset(sv_state* s, uint64_t basis_index);
+
+/* Applies gates[0..n_gates) in list order (validated first: SV_ERR_ARG for an
+ * unknown opcode or a non-finite angle, SV_ERR_QUBIT for a qubit outside
+ * 0..n-1 or a two-qubit gate with q0 == q1; nothing is applied then).
+ * The gates are fused into blocks of up to max_fuse_k qubits and grouped into
+ * tile passes (one HBM read and write of the state per pass).  Returns after
+ * the kernels have finished. */
+int sv_apply_circuit(sv_state* s, const sv_gate* gates, size_t n_gates,
+                     const sv_run_opts* opts);
+
+/* p_i = |a_i|^2 for all 2^n amplitudes, computed and written as float64
+ * (complex64 amplitudes are squared exactly, without first rounding to
+ * float32).  out_len must equal 2^n (else SV_ERR_SIZE).  out is host memory
+ * unless out_is_device.  Listing 3's probabilities() call. */
+int sv_probabilities(sv_state* s, double* out, size_t out_len, int out_is_device);
+
+/* Marginal distribution over the qubits set in qubit_mask: out[k] is the sum
+ * of p_i over every i whose masked bits, packed in ascending qubit order,
+ * equal k.  out_len must equal 2^popcount(mask).  The CutQC Builder's
+ * reconstruction over chosen qubits (Sec. IV-A, "Builder and Verifier"). */
+int sv_marginal_probabilities(sv_state* s, uint64_t qubit_mask, double* out,
+                              size_t out_len, int out_is_device);
+
+/* Copies the amplitudes (sv_state_bytes bytes, in the state's dtype) out, or
+ * in (sv_set_amplitudes: checkpoint restore). */
+int sv_amplitudes(sv_state* s, void* out, size_t bytes, int out_is_device);
+int sv_set_amplitudes(sv_state* s, const void* in, size_t bytes, int in_is_device);
+
+/* sum_i |a_i|^2, accumulated exactly in 128-bit fixed point on the device
+ * (order-independent, so bitwise reproducible) and rounded once to float64. */
+int sv_norm(sv_state* s, double* out);
+
+/* Statistics of the last sv_apply_circuit on this handle. */
+typedef struct {
+    int32_t n_blocks;        /* fused blocks                                */
+    int32_t n_passes;        /* tile passes = HBM read+write sweeps         */
+    int32_t fuse_k;          /* fusion width used                           */
+    int32_t tile_qubits;     /* tile qubits used                            */
+    int32_t arith;           /* sv_arith used                               */
+    int32_t n_launches;      /* kernels launched                            */
+    double  flops;           /* modelled arithmetic, real flops             */
+    double  hbm_bytes;       /* passes x 2 x state bytes                    */
+    double  plan_ms;         /* host planning time                          */
+} sv_apply_stats;
+int sv_last_stats(const sv_state* s, sv_apply_stats* out);
+
+/* Batched form: simulates every item from |0...0> (each its own width and
+ * dtype) and writes its full probability vector (2^n float64) to probs_out.
+ * Items are grouped by plan shape and run as multi-state launches captured
+ * in one CUDA graph; states stay resident in a pooled device arena.
+ * item_status[i] receives each item's sv_status (may be NULL). */
+typedef struct {
+    int32_t n_qubits;
+    int32_t dt;
+    const sv_gate* gates;
+    size_t n_gates;
+    double* probs_out;
+    int32_t probs_on_device;
+} sv_batch_item;
+int sv_batch_run(const sv_batch_item* items, size_t n_items,
+                 const sv_run_opts* opts, int* item_status);
+
+/* Static description of a status code. */
+const char* sv_status_str(int status);
+
+/* Library version string. */
+const char* sv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBSV_SV_H */

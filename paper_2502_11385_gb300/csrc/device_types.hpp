@@ -1,0 +1,33 @@
+// Descriptors shared by the host launcher and the sm_103a kernels.
+#pragma once
+#include <cstdint>
+
+namespace svk {
+
+constexpr int kMaxQ = 40;
+
+enum OpKind : int32_t { OP_DENSE = 0, OP_DIAG = 1 };
+enum OpFlags : int32_t { OPF_SIGN_ONLY = 1 };
+
+// One fused block inside a tile pass (64 bytes).
+struct alignas(16) DevOp {
+    int32_t kind;     // OpKind
+    int32_t k;        // qubits of the block (1..5)
+    int32_t coeff;    // offset of its coefficients (complex elements)
+    int32_t flags;    // OpFlags
+    int32_t pos[5];   // dense: tile positions, ascending; diag: tile position or -1
+    int32_t qbit[5];  // diag: global qubit of matrix bit j
+    int32_t pad[2];
+};
+
+// One tile pass: the tile holds the qubits L[0..m) (ascending, L[j] = j for
+// j < c), the other n - m qubits NL[] index the tiles.
+struct DevPass {
+    int32_t n, m, c, n_ops;
+    int32_t op0, kmax;    // first op; largest dense block of the pass
+    uint64_t tile_count;  // 2^(n-m)
+    int8_t L[kMaxQ];
+    int8_t NL[kMaxQ];
+};
+
+}  // namespace svk

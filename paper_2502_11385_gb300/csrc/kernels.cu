@@ -1,0 +1,455 @@
+// sm_103a kernels of the statevector engine.
+//
+//   K1 k_init          amp := e_basis
+//   K5 k_tile_pass     cache-blocked pass: gather a tile of 2^m amplitudes over
+//                      the pass's local qubits into shared memory, apply the
+//                      pass's fused blocks in order, write the tile back
+//                      (the single-GPU counterpart of Aer's chunk blocking,
+//                      Sec. III-B, Fig. 4)
+//   K7 k_probs         p_i = |a_i|^2 (Listing 3's probabilities())
+//      k_norm_*        sum_i p_i, exact 128-bit fixed-point accumulation
+//      k_marginal      marginal distribution over chosen qubits (the
+//                      Builder's partial reconstruction, Sec. IV-A)
+//
+// Amplitudes are interleaved complex; index bit q is qubit q.
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "sv.h"
+
+namespace svk {
+
+template <typename R>
+struct alignas(2 * sizeof(R)) Cx {
+    R re, im;
+};
+
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of a tile: 16-byte slots, XOR-swizzled so that warps
+// gathering amplitudes at power-of-two strides spread over the banks.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int swz(int j) {
+    constexpr int VS = (sizeof(R) == 4) ? 1 : 0;  // log2(amplitudes per 16-byte slot)
+    int s = j >> VS;
+    int h = (s >> 3) ^ (s >> 6) ^ (s >> 9) ^ (s >> 12);
+    s ^= h & 7;
+    return (s << VS) | (j & ((1 << VS) - 1));
+}
+
+// ---------------------------------------------------------------------------
+// K1: initialise to a basis state.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ int4 unit_vector16(int e);  // 16 bytes holding 1 at amplitude e, 0 elsewhere
+template <>
+__device__ __forceinline__ int4 unit_vector16<float>(int e) {
+    const int one = __float_as_int(1.0f);
+    return e == 0 ? make_int4(one, 0, 0, 0) : make_int4(0, 0, one, 0);
+}
+template <>
+__device__ __forceinline__ int4 unit_vector16<double>(int) {
+    const long long one = __double_as_longlong(1.0);
+    return make_int4((int)(one & 0xffffffffll), (int)(one >> 32), 0, 0);
+}
+
+template <typename R>
+__global__ void k_init(Cx<R>* __restrict__ a, uint64_t dim, uint64_t basis) {
+    constexpr int PER = 16 / sizeof(Cx<R>);  // amplitudes per 16-byte store; dim is a multiple
+    const uint64_t nvec = dim / PER;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride) {
+        const int4 z = (basis / PER == v) ? unit_vector16<R>((int)(basis % PER)) : make_int4(0, 0, 0, 0);
+        reinterpret_cast<int4*>(a)[v] = z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5: tile pass.
+// ---------------------------------------------------------------------------
+// Offset of matrix row/column b inside a group: bit j of b selects tile
+// position pos[j] (pm[j] = 1 << pos[j]).
+template <int K>
+__device__ __forceinline__ int group_offset(int b, const int (&pm)[K]) {
+    int off = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++)
+        if ((b >> j) & 1) off |= pm[j];
+    return off;
+}
+
+template <int K, typename R>
+__device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, const Cx<R>* __restrict__ M) {
+    constexpr int D = 1 << K;
+    int pos[K], pm[K];
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        pos[j] = op.pos[j];
+        pm[j] = 1 << pos[j];
+    }
+    const int ng = 1 << (m - K);
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        int base = g;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            const int p = pos[j];
+            base = ((base >> p) << (p + 1)) | (base & ((1 << p) - 1));
+        }
+        Cx<R> a[D];
+#pragma unroll
+        for (int b = 0; b < D; b++) a[b] = sm[swz<R>(base | group_offset<K>(b, pm))];
+#pragma unroll(K <= 2 ? D : 1)
+        for (int r = 0; r < D; r++) {
+            R re = R(0), im = R(0);
+#pragma unroll
+            for (int c = 0; c < D; c++) {
+                const Cx<R> u = M[r * D + c];
+                re = fmaT(u.re, a[c].re, re);
+                re = fmaT(-u.im, a[c].im, re);
+                im = fmaT(u.re, a[c].im, im);
+                im = fmaT(u.im, a[c].re, im);
+            }
+            sm[swz<R>(base | group_offset<K>(r, pm))] = Cx<R>{re, im};
+        }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void op_diag(Cx<R>* sm, int m, const DevOp& op, const Cx<R>* __restrict__ M,
+                                        uint64_t tile_base) {
+    int cidx = 0, lp[5], lb[5], nl = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        if (j < op.k) {
+            if (op.pos[j] < 0) {
+                cidx |= (int)((tile_base >> op.qbit[j]) & 1) << j;
+            } else {
+                lp[nl] = op.pos[j];
+                lb[nl] = j;
+                nl++;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 5; j++)
+        if (j >= nl) { lp[j] = 0; lb[j] = 31; }  // contributes nothing (bit shifted out)
+    const int N = 1 << m;
+    const bool sign_only = op.flags & OPF_SIGN_ONLY;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        int idx = cidx;
+#pragma unroll
+        for (int j = 0; j < 5; j++) idx |= (lb[j] < 31) ? (((i >> lp[j]) & 1) << lb[j]) : 0;
+        const Cx<R> u = M[idx];
+        const int s = swz<R>(i);
+        Cx<R> a = sm[s];
+        if (sign_only) {
+            if (u.re < R(0)) sm[s] = Cx<R>{-a.re, -a.im};
+        } else {
+            sm[s] = Cx<R>{fmaT(u.re, a.re, -u.im * a.im), fmaT(u.re, a.im, u.im * a.re)};
+        }
+    }
+}
+
+template <typename R, int KMAX>
+__global__ void __launch_bounds__(kTileThreads) k_tile_pass(Cx<R>* __restrict__ st, const DevPass P,
+                                                            const DevOp* __restrict__ ops,
+                                                            const Cx<R>* __restrict__ coef) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Cx<R>* sm = reinterpret_cast<Cx<R>*>(smraw);
+    __shared__ uint64_t dep[2][32];  // deposit tables for the tile's high local bits
+    const int m = P.m, c = P.c, hb = m - c;
+    if (threadIdx.x < 64) {
+        const int w = threadIdx.x >> 5, v = threadIdx.x & 31;
+        uint64_t d = 0;
+        for (int b = 0; b < 5; b++) {
+            const int bit = w * 5 + b;
+            if (bit < hb && ((v >> b) & 1)) d |= 1ull << P.L[c + bit];
+        }
+        dep[w][v] = d;
+    }
+    __syncthreads();
+    constexpr int PER = 16 / sizeof(Cx<R>);      // amplitudes per 16-byte vector
+    const int nvec = (1 << m) / PER;
+    const int cmask = (1 << c) - 1;
+    for (uint64_t t = blockIdx.x; t < P.tile_count; t += gridDim.x) {
+        uint64_t base = 0;
+        for (int b = 0; b < P.n - m; b++)
+            if ((t >> b) & 1) base |= 1ull << P.NL[b];
+        // gather: runs of 2^c contiguous amplitudes
+        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+            const int j = v * PER;
+            const int r = j >> c;
+            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+            const int4 val = *reinterpret_cast<const int4*>(st + gidx);
+            *reinterpret_cast<int4*>(sm + swz<R>(j)) = val;
+        }
+        __syncthreads();
+        for (int o = 0; o < P.n_ops; o++) {
+            const DevOp op = ops[P.op0 + o];
+            const Cx<R>* M = coef + op.coeff;
+            if (op.kind == OP_DIAG) {
+                op_diag<R>(sm, m, op, M, base);
+            } else {
+                if (op.k == 1) op_dense<1, R>(sm, m, op, M);
+                else if (op.k == 2) op_dense<(KMAX >= 2 ? 2 : 1), R>(sm, m, op, M);
+                else if (op.k == 3) op_dense<(KMAX >= 3 ? 3 : 1), R>(sm, m, op, M);
+                else if (op.k == 4) op_dense<(KMAX >= 4 ? 4 : 1), R>(sm, m, op, M);
+                else op_dense<(KMAX >= 5 ? 5 : 1), R>(sm, m, op, M);
+            }
+            __syncthreads();
+        }
+        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+            const int j = v * PER;
+            const int r = j >> c;
+            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+            *reinterpret_cast<int4*>(st + gidx) = *reinterpret_cast<const int4*>(sm + swz<R>(j));
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K7: probabilities, exact norm, marginals.
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ double prob_of(Cx<R> v) {
+    const double re = (double)v.re, im = (double)v.im;
+    return fma(re, re, im * im);  // exact products for float inputs, one rounding
+}
+
+// x >= 0 (x < 16) as an unsigned 128-bit fixed-point number in units of 2^-124.
+__device__ __forceinline__ unsigned __int128 to_fixed(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;  // zero or subnormal (below 2^-1022): below the grid
+    const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = e - 1075 + 124;
+    if (sh >= 0) return (unsigned __int128)mant << sh;
+    if (sh <= -53) return 0;
+    return (unsigned __int128)(mant >> (-sh));
+}
+
+__device__ __forceinline__ double fixed_to_double(unsigned __int128 v) {
+    if (v == 0) return 0.0;
+    const unsigned long long hi = (unsigned long long)(v >> 64), lo = (unsigned long long)v;
+    const int lz = hi ? __clzll(hi) : 64 + __clzll(lo);
+    const unsigned __int128 nv = v << lz;
+    unsigned long long top = (unsigned long long)(nv >> 64);
+    top |= ((unsigned long long)nv != 0ull) ? 1ull : 0ull;  // sticky bit
+    return ldexp(__ull2double_rn(top), 64 - lz - 124);
+}
+
+__device__ __forceinline__ unsigned __int128 warp_sum128(unsigned __int128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+        const unsigned long long lo2 = __shfl_down_sync(0xffffffffu, lo, o);
+        const unsigned long long hi2 = __shfl_down_sync(0xffffffffu, hi, o);
+        v += ((unsigned __int128)hi2 << 64) | lo2;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned __int128 block_sum128(unsigned __int128 v) {
+    __shared__ unsigned long long red[2][32];
+    v = warp_sum128(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][w] = (unsigned long long)v;
+        red[1][w] = (unsigned long long)(v >> 64);
+    }
+    __syncthreads();
+    unsigned __int128 r = 0;
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        if (lane < nw) r = ((unsigned __int128)red[1][lane] << 64) | red[0][lane];
+        r = warp_sum128(r);
+    }
+    return r;  // valid in thread 0
+}
+
+template <typename R>
+__global__ void k_probs(const Cx<R>* __restrict__ a, uint64_t i0, uint64_t len, double* __restrict__ p) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride)
+        p[i] = prob_of<R>(a[i0 + i]);
+}
+
+template <typename R>
+__global__ void k_norm_partial(const Cx<R>* __restrict__ a, uint64_t dim, unsigned long long* __restrict__ part) {
+    unsigned __int128 acc = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride)
+        acc += to_fixed(prob_of<R>(a[i]));
+    acc = block_sum128(acc);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = (unsigned long long)acc;
+        part[2 * blockIdx.x + 1] = (unsigned long long)(acc >> 64);
+    }
+}
+
+__global__ void k_norm_final(const unsigned long long* __restrict__ part, int nparts, double* out) {
+    unsigned __int128 acc = 0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x)
+        acc += ((unsigned __int128)part[2 * i + 1] << 64) | part[2 * i];
+    acc = block_sum128(acc);
+    if (threadIdx.x == 0) *out = fixed_to_double(acc);
+}
+
+struct MaskInfo {
+    int32_t nq;
+    int8_t q[kMaxQ];
+};
+
+__device__ __forceinline__ void atomic_add128(unsigned long long* bin, unsigned __int128 v) {
+    const unsigned long long lo = (unsigned long long)v;
+    unsigned long long hi = (unsigned long long)(v >> 64);
+    const unsigned long long old = atomicAdd(bin, lo);
+    if (old + lo < old) hi += 1ull;  // carry out of the low word
+    if (hi) atomicAdd(bin + 1, hi);
+}
+
+template <typename R>
+__global__ void k_marginal(const Cx<R>* __restrict__ a, uint64_t dim, const MaskInfo mi,
+                           unsigned long long* __restrict__ gbins, int nbins, int use_smem) {
+    extern __shared__ unsigned long long sbins[];
+    if (use_smem) {
+        for (int b = threadIdx.x; b < 2 * nbins; b += blockDim.x) sbins[b] = 0ull;
+        __syncthreads();
+    }
+    unsigned long long* bins = use_smem ? sbins : gbins;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+        int k = 0;
+        for (int j = 0; j < mi.nq; j++) k |= (int)((i >> mi.q[j]) & 1) << j;
+        const unsigned __int128 fx = to_fixed(prob_of<R>(a[i]));
+        if (fx) atomic_add128(bins + 2 * k, fx);
+    }
+    if (use_smem) {
+        __syncthreads();
+        for (int b = threadIdx.x; b < nbins; b += blockDim.x) {
+            const unsigned __int128 v = ((unsigned __int128)sbins[2 * b + 1] << 64) | sbins[2 * b];
+            if (v) atomic_add128(gbins + 2 * b, v);
+        }
+    }
+}
+
+__global__ void k_bins_to_double(const unsigned long long* __restrict__ bins, uint64_t nbins, double* out) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; b < nbins; b += stride)
+        out[b] = fixed_to_double(((unsigned __int128)bins[2 * b + 1] << 64) | bins[2 * b]);
+}
+
+__global__ void k_zero_u64(unsigned long long* p, uint64_t n) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = 0ull;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+static unsigned grid_for(uint64_t work, int threads, const DevInfo& di, int per_sm = 8) {
+    uint64_t g = (work + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)di.sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+cudaError_t launch_init(int dt, void* amp, int n, uint64_t basis, cudaStream_t s, const DevInfo& di) {
+    const uint64_t dim = 1ull << n;
+    if (dt == SV_C64)
+        k_init<float><<<grid_for(dim / 2, 256, di), 256, 0, s>>>((Cx<float>*)amp, dim, basis);
+    else
+        k_init<double><<<grid_for(dim, 256, di), 256, 0, s>>>((Cx<double>*)amp, dim, basis);
+    return cudaGetLastError();
+}
+
+template <typename R, int KMAX>
+static cudaError_t tile_pass_impl(void* amp, const DevPass& p, const DevOp* d_ops, const void* d_coef,
+                                  cudaStream_t s, const DevInfo& di) {
+    const size_t smem = ((size_t)1 << p.m) * sizeof(Cx<R>);
+    static int configured_dev = -1;
+    if (configured_dev != di.device) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_pass<R, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(di.smem_optin - 2048));
+        if (e != cudaSuccess) return e;
+        configured_dev = di.device;
+    }
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<R, KMAX>, kTileThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (uint64_t)di.sms * per_sm;
+    if (grid > p.tile_count) grid = p.tile_count;
+    k_tile_pass<R, KMAX><<<(unsigned)grid, kTileThreads, smem, s>>>((Cx<R>*)amp, p, d_ops, (const Cx<R>*)d_coef);
+    return cudaGetLastError();
+}
+
+template <typename R>
+static cudaError_t tile_pass_k(int kmax, void* amp, const DevPass& p, const DevOp* d_ops, const void* d_coef,
+                               cudaStream_t s, const DevInfo& di) {
+    switch (kmax) {
+        case 1: return tile_pass_impl<R, 1>(amp, p, d_ops, d_coef, s, di);
+        case 2: return tile_pass_impl<R, 2>(amp, p, d_ops, d_coef, s, di);
+        case 3: return tile_pass_impl<R, 3>(amp, p, d_ops, d_coef, s, di);
+        case 4: return tile_pass_impl<R, 4>(amp, p, d_ops, d_coef, s, di);
+        default: return tile_pass_impl<R, 5>(amp, p, d_ops, d_coef, s, di);
+    }
+}
+
+cudaError_t launch_tile_pass(int dt, int arith, void* amp, const DevPass& p, const DevOp* d_ops,
+                             const void* d_coef, cudaStream_t s, const DevInfo& di) {
+    (void)arith;
+    if (dt == SV_C64) return tile_pass_k<float>(p.kmax, amp, p, d_ops, d_coef, s, di);
+    return tile_pass_k<double>(p.kmax, amp, p, d_ops, d_coef, s, di);
+}
+
+cudaError_t launch_probs(int dt, const void* amp, uint64_t i0, uint64_t len, double* p, cudaStream_t s,
+                         const DevInfo& di) {
+    if (dt == SV_C64)
+        k_probs<float><<<grid_for(len, 256, di), 256, 0, s>>>((const Cx<float>*)amp, i0, len, p);
+    else
+        k_probs<double><<<grid_for(len, 256, di), 256, 0, s>>>((const Cx<double>*)amp, i0, len, p);
+    return cudaGetLastError();
+}
+
+static constexpr int kNormThreads = 256;
+size_t norm_scratch_bytes(const DevInfo& di) { return (size_t)di.sms * 8 * 2 * sizeof(unsigned long long); }
+
+cudaError_t launch_norm(int dt, const void* amp, int n, void* d_scratch, double* d_out, cudaStream_t s,
+                        const DevInfo& di) {
+    const uint64_t dim = 1ull << n;
+    const unsigned grid = grid_for(dim, kNormThreads, di, 8);
+    auto* part = (unsigned long long*)d_scratch;
+    if (dt == SV_C64)
+        k_norm_partial<float><<<grid, kNormThreads, 0, s>>>((const Cx<float>*)amp, dim, part);
+    else
+        k_norm_partial<double><<<grid, kNormThreads, 0, s>>>((const Cx<double>*)amp, dim, part);
+    k_norm_final<<<1, 1024, 0, s>>>(part, (int)grid, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_marginal(int dt, const void* amp, int n, uint64_t qubit_mask, void* d_bins, double* d_out,
+                            cudaStream_t s, const DevInfo& di) {
+    MaskInfo mi{};
+    for (int q = 0; q < n; q++)
+        if ((qubit_mask >> q) & 1) mi.q[mi.nq++] = (int8_t)q;
+    const uint64_t nbins = 1ull << mi.nq, dim = 1ull << n;
+    auto* bins = (unsigned long long*)d_bins;
+    k_zero_u64<<<grid_for(2 * nbins, 256, di), 256, 0, s>>>(bins, 2 * nbins);
+    const int use_smem = nbins <= 2048 ? 1 : 0;
+    const size_t smem = use_smem ? 2 * nbins * sizeof(unsigned long long) : 0;
+    const unsigned grid = grid_for(dim, 256, di, 4);
+    if (dt == SV_C64)
+        k_marginal<float><<<grid, 256, smem, s>>>((const Cx<float>*)amp, dim, mi, bins, (int)nbins, use_smem);
+    else
+        k_marginal<double><<<grid, 256, smem, s>>>((const Cx<double>*)amp, dim, mi, bins, (int)nbins, use_smem);
+    k_bins_to_double<<<grid_for(nbins, 256, di), 256, 0, s>>>(bins, nbins, d_out);
+    return cudaGetLastError();
+}
+
+}  // namespace svk

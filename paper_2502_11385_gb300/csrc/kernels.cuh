@@ -1,0 +1,45 @@
+// Launchers of the sm_103a kernels (C++ linkage, used by the C-ABI layer).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "device_types.hpp"
+
+namespace svk {
+
+struct DevInfo {
+    int device = 0;
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+
+// Tile-pass kernel configuration.
+constexpr int kTileThreads = 256;
+
+// amp := e_basis (K1).
+cudaError_t launch_init(int dt, void* amp, int n, uint64_t basis, cudaStream_t s, const DevInfo& di);
+
+// One tile pass (K5): every tile of the state is gathered into shared memory,
+// the pass's ops are applied in order, and the tile is written back.
+// arith: SV_ARITH_NATIVE or SV_ARITH_DF64 (complex128 only).
+cudaError_t launch_tile_pass(int dt, int arith, void* amp, const DevPass& p, const DevOp* d_ops,
+                             const void* d_coef, cudaStream_t s, const DevInfo& di);
+
+// p[i - i0] = |amp_i|^2 for i in [i0, i0 + len) (K7, probability part).
+cudaError_t launch_probs(int dt, const void* amp, uint64_t i0, uint64_t len, double* p,
+                         cudaStream_t s, const DevInfo& di);
+
+// *d_out = sum_i |amp_i|^2 via exact 128-bit fixed-point accumulation (K7, norm part).
+// d_scratch needs norm_scratch_bytes(di) bytes.
+size_t norm_scratch_bytes(const DevInfo& di);
+cudaError_t launch_norm(int dt, const void* amp, int n, void* d_scratch, double* d_out,
+                        cudaStream_t s, const DevInfo& di);
+
+// Marginal over the qubits of qubit_mask into d_out (2^popcount doubles);
+// d_bins needs 2 * 8 * 2^popcount bytes.
+cudaError_t launch_marginal(int dt, const void* amp, int n, uint64_t qubit_mask, void* d_bins,
+                            double* d_out, cudaStream_t s, const DevInfo& di);
+
+}  // namespace svk

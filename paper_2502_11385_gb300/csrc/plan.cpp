@@ -1,0 +1,311 @@
+// Host planner: gate matrices, fusion, tile-pass scheduling, cost model.
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace svp {
+
+namespace {
+inline int popc(uint64_t x) { return __builtin_popcountll(x); }
+const double kPi = 3.14159265358979323846264338327950288;
+}  // namespace
+
+int gate_arity(int op) {
+    if (op < 0 || op >= SV_NUM_OPS) return 0;
+    return op >= SV_CX ? 2 : 1;
+}
+
+bool gate_is_diagonal(int op) {
+    return op == SV_Z || op == SV_S || op == SV_T || op == SV_RZ || op == SV_CZ || op == SV_RZZ;
+}
+
+void gate_matrix(const sv_gate& g, cd* m) {
+    const cd I(0, 1);
+    const int d = 1 << gate_arity(g.op);
+    for (int i = 0; i < d * d; i++) m[i] = 0;
+    const double c = std::cos(g.theta / 2), s = std::sin(g.theta / 2);
+    const double r2 = 1.0 / std::sqrt(2.0);
+    auto ph = [](double a) { return cd(std::cos(a), std::sin(a)); };
+    switch (g.op) {
+        case SV_H: m[0] = r2; m[1] = r2; m[2] = r2; m[3] = -r2; break;
+        case SV_X: m[1] = 1; m[2] = 1; break;
+        case SV_Y: m[1] = -I; m[2] = I; break;
+        case SV_Z: m[0] = 1; m[3] = -1; break;
+        case SV_S: m[0] = 1; m[3] = I; break;
+        case SV_T: m[0] = 1; m[3] = ph(kPi / 4); break;
+        case SV_RX: m[0] = c; m[1] = -I * s; m[2] = -I * s; m[3] = c; break;
+        case SV_RY: m[0] = c; m[1] = -s; m[2] = s; m[3] = c; break;
+        case SV_RZ: m[0] = ph(-g.theta / 2); m[3] = ph(g.theta / 2); break;
+        case SV_U3:
+            m[0] = c;
+            m[1] = -ph(g.lambda) * s;
+            m[2] = ph(g.phi) * s;
+            m[3] = ph(g.phi + g.lambda) * c;
+            break;
+        case SV_CX:  // local index b(q0) + 2 b(q1); flips b(q1) when b(q0) = 1
+            for (int a = 0; a < 4; a++) {
+                int b0 = a & 1, b1 = a >> 1;
+                m[(b0 | ((b1 ^ b0) << 1)) * 4 + a] = 1;
+            }
+            break;
+        case SV_CZ: m[0] = 1; m[5] = 1; m[10] = 1; m[15] = -1; break;
+        case SV_RZZ: {
+            cd a = ph(-g.theta / 2), b = ph(g.theta / 2);
+            m[0] = a; m[5] = b; m[10] = b; m[15] = a;
+            break;
+        }
+        case SV_SWAP:
+            for (int a = 0; a < 4; a++) {
+                int b0 = a & 1, b1 = a >> 1;
+                m[(b1 | (b0 << 1)) * 4 + a] = 1;
+            }
+            break;
+        default: break;
+    }
+}
+
+int validate(int n, const sv_gate* g, size_t ng) {
+    if (ng && !g) return SV_ERR_ARG;
+    for (size_t t = 0; t < ng; t++) {
+        int k = gate_arity(g[t].op);
+        if (k == 0) return SV_ERR_ARG;
+        if (!std::isfinite(g[t].theta) || !std::isfinite(g[t].phi) || !std::isfinite(g[t].lambda))
+            return SV_ERR_ARG;
+        if (g[t].q0 < 0 || g[t].q0 >= n) return SV_ERR_QUBIT;
+        if (k == 2 && (g[t].q1 < 0 || g[t].q1 >= n || g[t].q1 == g[t].q0)) return SV_ERR_QUBIT;
+    }
+    return SV_OK;
+}
+
+static uint64_t gate_mask(const sv_gate& g) {
+    uint64_t m = 1ull << g.q0;
+    if (gate_arity(g.op) == 2) m |= 1ull << g.q1;
+    return m;
+}
+
+static void set_qubits(Block& b) {
+    b.k = 0;
+    for (int q = 0; q < 64; q++)
+        if ((b.mask >> q) & 1) b.qubits[b.k++] = q;
+}
+
+std::vector<Block> fuse(int n, const sv_gate* g, size_t ng, int fuse_k) {
+    std::vector<Block> blocks;
+    std::vector<int> cur(n, -1);  // latest block holding each qubit
+    for (size_t t = 0; t < ng; t++) {
+        const uint64_t gm = gate_mask(g[t]);
+        int bstar = -1;
+        for (int q = 0; q < n; q++)
+            if ((gm >> q) & 1) bstar = std::max(bstar, cur[q]);
+        if (fuse_k > 1 && bstar >= 0 && popc(blocks[bstar].mask | gm) <= fuse_k) {
+            blocks[bstar].mask |= gm;
+            blocks[bstar].gates.push_back((int)t);
+        } else {
+            Block b;
+            b.mask = gm;
+            b.gates.push_back((int)t);
+            blocks.push_back(b);
+            bstar = (int)blocks.size() - 1;
+        }
+        for (int q = 0; q < n; q++)
+            if ((gm >> q) & 1) cur[q] = bstar;
+    }
+    for (auto& b : blocks) {
+        set_qubits(b);
+        bool diag = true;
+        for (int t : b.gates) diag = diag && gate_is_diagonal(g[t].op);
+        b.kind = diag ? BK_DIAG : BK_DENSE;
+    }
+    return blocks;
+}
+
+// Embeds gate g (acting on its own local index) into the block's 2^k space and
+// left-multiplies: M <- G_emb * M.
+static void left_multiply(Block& b, const sv_gate& g, std::vector<cd>& M) {
+    const int k = b.k, D = 1 << k;
+    cd gm[16];
+    gate_matrix(g, gm);
+    const int ga = gate_arity(g.op);
+    int gp[2] = {0, 0};  // block-local bit of the gate's qubits
+    for (int j = 0; j < k; j++) {
+        if (b.qubits[j] == g.q0) gp[0] = j;
+        if (ga == 2 && b.qubits[j] == g.q1) gp[1] = j;
+    }
+    const int gd = 1 << ga;
+    std::vector<cd> out((size_t)D * D, cd(0, 0));
+    for (int r = 0; r < D; r++) {
+        // row r of G_emb: nonzero only at columns c equal to r outside the gate bits
+        int lr = 0;
+        for (int a = 0; a < ga; a++) lr |= ((r >> gp[a]) & 1) << a;
+        int rbase = r;
+        for (int a = 0; a < ga; a++) rbase &= ~(1 << gp[a]);
+        for (int lc = 0; lc < gd; lc++) {
+            cd coef = gm[lr * gd + lc];
+            if (coef == cd(0, 0)) continue;
+            int c = rbase;
+            for (int a = 0; a < ga; a++) c |= ((lc >> a) & 1) << gp[a];
+            for (int col = 0; col < D; col++) out[(size_t)r * D + col] += coef * M[(size_t)c * D + col];
+        }
+    }
+    M.swap(out);
+}
+
+void finalize(std::vector<Block>& blocks, const sv_gate* g) {
+    for (auto& b : blocks) {
+        const int D = 1 << b.k;
+        std::vector<cd> M((size_t)D * D, cd(0, 0));
+        for (int i = 0; i < D; i++) M[(size_t)i * D + i] = 1;
+        for (int t : b.gates) left_multiply(b, g[t], M);
+        if (b.kind == BK_DIAG) {
+            b.mat.resize(D);
+            bool sign = true;
+            for (int i = 0; i < D; i++) {
+                b.mat[i] = M[(size_t)i * D + i];
+                sign = sign && b.mat[i].imag() == 0.0 && std::fabs(b.mat[i].real()) == 1.0;
+            }
+            b.sign_only = sign;
+        } else {
+            b.mat.swap(M);
+        }
+    }
+}
+
+std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, int coalesce) {
+    std::vector<Pass> passes;
+    const size_t nb = blocks.size();
+    std::vector<char> done(nb, 0);
+    size_t first = 0;  // first block not yet done
+    const uint64_t all = (n >= 64) ? ~0ull : ((1ull << n) - 1);
+    if (tile_m >= n) {
+        Pass p;
+        p.local_mask = all;
+        p.m = n;
+        for (size_t b = 0; b < nb; b++) p.blocks.push_back((int)b);
+        if (nb) passes.push_back(p);
+        return passes;
+    }
+    const uint64_t low = (1ull << std::min(coalesce, n)) - 1;
+    while (first < nb) {
+        Pass p;
+        uint64_t local = low, blocked = 0;
+        for (size_t b = first; b < nb; b++) {
+            if (done[b]) continue;
+            const Block& B = blocks[b];
+            if (B.mask & blocked) { blocked |= B.mask; continue; }
+            if (B.kind == BK_DIAG) { p.blocks.push_back((int)b); done[b] = 1; continue; }
+            uint64_t need = local | B.mask;
+            if (popc(need) <= tile_m) {
+                local = need;
+                p.blocks.push_back((int)b);
+                done[b] = 1;
+            } else {
+                blocked |= B.mask;
+            }
+            if ((blocked | local) == all && popc(local) == tile_m) {
+                // every qubit is either blocked or local and the tile is full:
+                // only diagonal blocks on unblocked qubits could still join
+                continue;
+            }
+        }
+        // fill the tile up to tile_m qubits with the lowest unused qubits
+        for (int q = 0; q < n && popc(local) < tile_m; q++) local |= 1ull << q;
+        p.local_mask = local;
+        p.m = popc(local);
+        passes.push_back(p);
+        while (first < nb && done[first]) first++;
+    }
+    return passes;
+}
+
+static double block_flops(const Block& b, double dim) {
+    // real flops (FMA = 2) applied to the whole 2^n state
+    if (b.kind == BK_DIAG) return b.sign_only ? 0.0 : 6.0 * dim;
+    return 8.0 * (double)(1 << b.k) * dim;
+}
+
+double model_cost(const Plan& p, int amp_bytes, bool fp64_alu, const Machine& mc, double* flops) {
+    const double dim = std::ldexp(1.0, p.n);
+    const double state = dim * amp_bytes;
+    double total = 0, fl_all = 0;
+    for (const auto& ps : p.passes) {
+        double fl = 0, smem = 0;
+        for (int bi : ps.blocks) {
+            fl += block_flops(p.blocks[bi], dim);
+            smem += 2.0 * state;
+        }
+        fl_all += fl;
+        const double alu = fl / 2.0 / (fp64_alu ? mc.fp64_fma_ps : mc.fp32_fma_ps);
+        const double hbm = 2.0 * state / mc.hbm_Bps;
+        const double sm = smem / mc.smem_Bps;
+        total += std::max(std::max(alu, hbm), sm) + mc.launch_s;
+    }
+    if (flops) *flops = fl_all;
+    return total;
+}
+
+Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int coalesce,
+               int amp_bytes, bool fp64_alu, const Machine& mc) {
+    Plan best;
+    best.model_s = 1e300;
+    int k_lo = fuse_k > 0 ? fuse_k : 1, k_hi = fuse_k > 0 ? fuse_k : kMaxFuse;
+    for (int k = k_lo; k <= k_hi; k++) {
+        Plan p;
+        p.n = n;
+        p.fuse_k = k;
+        p.tile_m = std::min(tile_m, n);
+        p.coalesce = std::min(coalesce, n);
+        p.blocks = fuse(n, g, ng, k);
+        // sign_only is known before the matrices are formed: diagonal blocks
+        // made of CZ / Z gates only
+        for (auto& b : p.blocks) {
+            if (b.kind != BK_DIAG) continue;
+            bool s = true;
+            for (int t : b.gates) s = s && (g[t].op == SV_CZ || g[t].op == SV_Z);
+            b.sign_only = s;
+        }
+        p.passes = schedule(n, p.blocks, p.tile_m, p.coalesce);
+        double fl = 0;
+        p.model_s = model_cost(p, amp_bytes, fp64_alu, mc, &fl);
+        p.flops = fl;
+        if (p.model_s < best.model_s) best = std::move(p);
+    }
+    finalize(best.blocks, g);
+    double fl = 0;
+    best.model_s = model_cost(best, amp_bytes, fp64_alu, mc, &fl);
+    best.flops = fl;
+    return best;
+}
+
+int check_plan(const Plan& p, size_t ng, const sv_gate* g) {
+    std::vector<int> seen(ng, 0);
+    std::vector<int> last(p.n, -1);  // last gate index applied per qubit
+    std::vector<char> used(p.blocks.size(), 0);
+    for (const auto& ps : p.passes) {
+        if (popc(ps.local_mask) != ps.m) return 1;
+        for (int bi : ps.blocks) {
+            if (bi < 0 || bi >= (int)p.blocks.size() || used[bi]) return 2;
+            used[bi] = 1;
+            const Block& b = p.blocks[bi];
+            if (b.k < 1 || b.k > kMaxFuse) return 3;
+            if (b.kind == BK_DENSE && (b.mask & ~ps.local_mask)) return 4;
+            for (int t : b.gates) {
+                if (t < 0 || (size_t)t >= ng || seen[t]) return 5;
+                seen[t] = 1;
+                uint64_t gm = gate_mask(g[t]);
+                if (gm & ~b.mask) return 6;
+                for (int q = 0; q < p.n; q++) {
+                    if (!((gm >> q) & 1)) continue;
+                    if (last[q] > t) return 7;  // per-qubit order broken
+                    last[q] = t;
+                }
+            }
+        }
+    }
+    for (size_t t = 0; t < ng; t++)
+        if (!seen[t]) return 8;
+    return 0;
+}
+
+}  // namespace svp

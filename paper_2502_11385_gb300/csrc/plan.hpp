@@ -1,0 +1,91 @@
+// Host planner of the statevector engine: gate IR -> fused blocks -> tile passes.
+//
+// The paper hands gate application to Qiskit Aer, whose transpiler blocks the
+// gates so that runs of them act on a set of "local" qubits held in one chunk
+// (qubit reordering and noiseless swap insertion, Sec. III-B, Fig. 4).  On one
+// GB300 the chunk becomes a shared-memory tile: a pass streams every tile of
+// the state through shared memory once and applies, per tile, every block
+// whose qubits are all held in the tile.  Any qubit set can be the tile's, so
+// no swap gates are needed: a pass simply gathers a different set.
+#pragma once
+#include <complex>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "sv.h"
+
+namespace svp {
+
+using cd = std::complex<double>;
+
+constexpr int kMaxFuse = 5;        // largest fused block (qubits)
+constexpr int kMaxQubits = 34;
+
+int gate_arity(int op);            // 1, 2, or 0 for an unknown opcode
+bool gate_is_diagonal(int op);     // Z, S, T, RZ, CZ, RZZ
+// Row-major 2x2 or 4x4 matrix (two-qubit local index b(q0) + 2 b(q1)),
+// computed in float64 with the host libm.
+void gate_matrix(const sv_gate& g, cd* m);
+
+// Validates a gate list for an n-qubit register; SV_OK or the sv_status.
+int validate(int n, const sv_gate* g, size_t ng);
+
+enum BlockKind { BK_DENSE = 0, BK_DIAG = 1 };
+
+struct Block {
+    int kind = BK_DENSE;
+    int k = 0;
+    int qubits[kMaxFuse] = {0, 0, 0, 0, 0};  // ascending; matrix bit j <-> qubits[j]
+    uint64_t mask = 0;
+    std::vector<int> gates;                  // input indices, application order
+    std::vector<cd> mat;                     // dense: (2^k)^2 row-major; diag: 2^k
+    bool sign_only = false;                  // diag entries all +1 / -1
+};
+
+struct Pass {
+    uint64_t local_mask = 0;                 // qubits held in the tile
+    int m = 0;                               // popcount(local_mask)
+    std::vector<int> blocks;                 // application order
+};
+
+struct Plan {
+    int n = 0, fuse_k = 0, tile_m = 0, coalesce = 0;
+    std::vector<Block> blocks;
+    std::vector<Pass> passes;
+    double flops = 0;      // modelled real flops (FMA = 2)
+    double model_s = 0;    // modelled time
+};
+
+struct Machine {           // throughput model used by the autotuner
+    double hbm_Bps = 6.6e12;
+    double fp32_fma_ps = 3.2e13;
+    double fp64_fma_ps = 4.6e11;
+    double smem_Bps = 3.5e13;
+    double launch_s = 4e-6;
+};
+
+// Greedy fusion: each gate joins the latest block among those holding its
+// qubits when the union stays within fuse_k qubits; otherwise it opens a new
+// block.  fuse_k = 1 keeps every gate on its own.
+std::vector<Block> fuse(int n, const sv_gate* g, size_t ng, int fuse_k);
+
+// Fills Block::mat / kind / sign_only from the gates (float64 products).
+void finalize(std::vector<Block>& blocks, const sv_gate* g);
+
+// Groups blocks into tile passes of tile_m qubits whose lowest `coalesce`
+// qubits are always local (contiguous runs for coalesced loads).
+std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, int coalesce);
+
+// Modelled cost of a plan (seconds) for a state of `amp_bytes` per amplitude.
+double model_cost(const Plan& p, int amp_bytes, bool fp64_alu, const Machine& mc, double* flops);
+
+// Full planning with optional autotuning over fuse_k (0 = auto).
+Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int coalesce,
+               int amp_bytes, bool fp64_alu, const Machine& mc);
+
+// Checks plan invariants: every gate exactly once, per-qubit order kept,
+// block sizes, locality of dense blocks.  Returns 0 when valid.
+int check_plan(const Plan& p, size_t ng, const sv_gate* g);
+
+}  // namespace svp

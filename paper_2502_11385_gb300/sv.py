@@ -1,0 +1,308 @@
+"""ctypes binding of libsv (include/sv.h, include/sv_plan.h).
+
+Argument marshalling only: every step of the statevector path runs in the
+library's sm_103a kernels.  Importing this module loads the library and fails
+loudly when it has not been built; there is no CPU fallback.
+
+Names follow the C-ABI: ``create``, ``apply_circuit``, ``probabilities``,
+``marginal_probabilities``, ``amplitudes``, ``norm``, ``batch_run`` ...
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .workloads import GATE_DTYPE
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libsv.so")
+
+SV_OK, SV_ERR_ARG, SV_ERR_QUBIT, SV_ERR_OOM, SV_ERR_SIZE, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6, -7
+C64, C128 = 0, 1
+ARITH_AUTO, ARITH_NATIVE, ARITH_DF64 = 0, 1, 2
+DTYPES = {"c64": C64, "c128": C128, C64: C64, C128: C128}
+NP_DTYPE = {C64: np.complex64, C128: np.complex128}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libsv is not built ({LIB_PATH} missing): run __graft_entry__.build() "
+                      "or python paper_2502_11385_gb300/build.py; there is no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+
+class RunOpts(ctypes.Structure):
+    _fields_ = [("max_fuse_k", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
+                ("arith", ctypes.c_int32), ("debug_checks", ctypes.c_int32)]
+
+
+class ApplyStats(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
+                ("tile_qubits", ctypes.c_int32), ("arith", ctypes.c_int32), ("n_launches", ctypes.c_int32),
+                ("flops", ctypes.c_double), ("hbm_bytes", ctypes.c_double), ("plan_ms", ctypes.c_double)]
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int32), ("dt", ctypes.c_int32), ("gates", ctypes.c_void_p),
+                ("n_gates", ctypes.c_size_t), ("probs_out", ctypes.c_void_p), ("probs_on_device", ctypes.c_int32)]
+
+
+class PlanSummary(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
+                ("tile_qubits", ctypes.c_int32), ("flops", ctypes.c_double), ("model_ms", ctypes.c_double)]
+
+
+_vp, _sz, _i32, _u64, _dp = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
+_SIGS = {
+    "sv_state_bytes": ([_i32, _i32], _sz),
+    "sv_create": ([_i32, _i32, ctypes.POINTER(_vp)], _i32),
+    "sv_create_on": ([_vp, _sz, _i32, _i32, _vp, ctypes.POINTER(_vp)], _i32),
+    "sv_destroy": ([_vp], None),
+    "sv_num_qubits": ([_vp], _i32),
+    "sv_dtype_of": ([_vp], _i32),
+    "sv_device_ptr": ([_vp], _vp),
+    "sv_reset": ([_vp, _u64], _i32),
+    "sv_apply_circuit": ([_vp, _vp, _sz, ctypes.POINTER(RunOpts)], _i32),
+    "sv_probabilities": ([_vp, _dp, _sz, _i32], _i32),
+    "sv_marginal_probabilities": ([_vp, _u64, _dp, _sz, _i32], _i32),
+    "sv_amplitudes": ([_vp, _vp, _sz, _i32], _i32),
+    "sv_set_amplitudes": ([_vp, _vp, _sz, _i32], _i32),
+    "sv_norm": ([_vp, ctypes.POINTER(ctypes.c_double)], _i32),
+    "sv_last_stats": ([_vp, ctypes.POINTER(ApplyStats)], _i32),
+    "sv_batch_run": ([ctypes.POINTER(BatchItem), _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(ctypes.c_int)], _i32),
+    "sv_status_str": ([_i32], ctypes.c_char_p),
+    "sv_version": ([], ctypes.c_char_p),
+    "sv_plan_build": ([_i32, _i32, _vp, _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(_vp)], _i32),
+    "sv_plan_free": ([_vp], None),
+    "sv_plan_summary_get": ([_vp, ctypes.POINTER(PlanSummary)], _i32),
+    "sv_plan_block": ([_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                       ctypes.POINTER(_i32), ctypes.POINTER(_i32), _sz, ctypes.POINTER(ctypes.c_double), _sz], _i32),
+    "sv_plan_pass": ([_vp, _i32, ctypes.POINTER(_u64), ctypes.POINTER(_i32), ctypes.POINTER(_i32), _sz], _i32),
+    "sv_plan_check": ([_vp, _vp, _sz], _i32),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+EXPORTED = tuple(_SIGS)
+
+
+class SvError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {status_str(code)} ({code})")
+
+
+def status_str(code: int) -> str:
+    return _lib.sv_status_str(code).decode()
+
+
+def version() -> str:
+    return _lib.sv_version().decode()
+
+
+def _check(code, what):
+    if code != SV_OK:
+        raise SvError(code, what)
+
+
+def state_bytes(n: int, dtype) -> int:
+    return int(_lib.sv_state_bytes(n, DTYPES[dtype]))
+
+
+def as_gates(gates) -> np.ndarray:
+    g = np.ascontiguousarray(gates)
+    if g.dtype != GATE_DTYPE:
+        raise TypeError("gates must be a numpy array with workloads.GATE_DTYPE")
+    return g
+
+
+def run_opts(max_fuse_k=0, tile_qubits=0, arith=ARITH_AUTO, debug_checks=0):
+    return RunOpts(max_fuse_k, tile_qubits, arith, debug_checks)
+
+
+def _opts_ptr(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, dict):
+        opts = RunOpts(**opts)
+    return ctypes.byref(opts)
+
+
+def _ptr_of(buf):
+    """(pointer, is_device) for a numpy array or a torch tensor."""
+    if isinstance(buf, np.ndarray):
+        return buf.ctypes.data, 0
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr(), 1 if buf.is_cuda else 0
+    raise TypeError(type(buf))
+
+
+class State:
+    """An n-qubit statevector in device memory (sv_state)."""
+
+    def __init__(self, n: int, dtype="c128", _handle=None, _keep=None):
+        self.n = n
+        self.dt = DTYPES[dtype]
+        self._keep = _keep
+        if _handle is None:
+            h = _vp()
+            _check(_lib.sv_create(n, self.dt, ctypes.byref(h)), "sv_create")
+            _handle = h
+        self._h = _handle
+
+    @classmethod
+    def from_tensor(cls, tensor, n: int, dtype, stream=None):
+        """Wraps a caller-owned CUDA tensor (kept alive by the State)."""
+        dt = DTYPES[dtype]
+        h = _vp()
+        st = _vp(stream) if stream is not None else None
+        _check(_lib.sv_create_on(tensor.data_ptr(), tensor.numel() * tensor.element_size(), n, dt, st,
+                                 ctypes.byref(h)), "sv_create_on")
+        return cls(n, dt, _handle=h, _keep=tensor)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def dim(self):
+        return 1 << self.n
+
+    @property
+    def device_ptr(self) -> int:
+        return int(_lib.sv_device_ptr(self._h) or 0)
+
+    def reset(self, basis: int = 0):
+        _check(_lib.sv_reset(self._h, basis), "sv_reset")
+
+    def apply_circuit(self, gates, opts=None):
+        g = as_gates(gates)
+        _check(_lib.sv_apply_circuit(self._h, g.ctypes.data if len(g) else None, len(g), _opts_ptr(opts)),
+               "sv_apply_circuit")
+        return self
+
+    def stats(self) -> dict:
+        s = ApplyStats()
+        _check(_lib.sv_last_stats(self._h, ctypes.byref(s)), "sv_last_stats")
+        return {f: getattr(s, f) for f, _ in ApplyStats._fields_}
+
+    def probabilities(self, out=None):
+        if out is None:
+            out = np.empty(self.dim, dtype=np.float64)
+        p, dev = _ptr_of(out)
+        _check(_lib.sv_probabilities(self._h, p, self.dim, dev), "sv_probabilities")
+        return out
+
+    def marginal_probabilities(self, qubit_mask: int, out=None):
+        nb = 1 << bin(qubit_mask).count("1")
+        if out is None:
+            out = np.empty(nb, dtype=np.float64)
+        p, dev = _ptr_of(out)
+        _check(_lib.sv_marginal_probabilities(self._h, qubit_mask, p, nb, dev), "sv_marginal_probabilities")
+        return out
+
+    def amplitudes(self, out=None):
+        if out is None:
+            out = np.empty(self.dim, dtype=NP_DTYPE[self.dt])
+        p, dev = _ptr_of(out)
+        _check(_lib.sv_amplitudes(self._h, p, state_bytes(self.n, self.dt), dev), "sv_amplitudes")
+        return out
+
+    def set_amplitudes(self, src):
+        p, dev = _ptr_of(src)
+        _check(_lib.sv_set_amplitudes(self._h, p, state_bytes(self.n, self.dt), dev), "sv_set_amplitudes")
+
+    def norm(self) -> float:
+        v = ctypes.c_double()
+        _check(_lib.sv_norm(self._h, ctypes.byref(v)), "sv_norm")
+        return v.value
+
+
+def create(n: int, dtype="c128") -> State:
+    return State(n, dtype)
+
+
+def simulate(n: int, gates, dtype="c128", opts=None):
+    """Full-circuit execution: |0..0> -> circuit -> (amplitudes, probabilities)."""
+    with State(n, dtype) as s:
+        s.apply_circuit(gates, opts)
+        return s.amplitudes(), s.probabilities()
+
+
+def batch_run(items, opts=None):
+    """items: list of (n, dtype, gates, probs_out or None).  Returns (outputs, statuses)."""
+    arr = (BatchItem * len(items))()
+    keep, outs = [], []
+    for i, (n, dtype, gates, out) in enumerate(items):
+        g = as_gates(gates)
+        if out is None:
+            out = np.empty(1 << n, dtype=np.float64)
+        p, dev = _ptr_of(out)
+        keep.append(g)
+        outs.append(out)
+        arr[i] = BatchItem(n, DTYPES[dtype], g.ctypes.data if len(g) else None, len(g), p, dev)
+    st = (ctypes.c_int * len(items))()
+    _lib.sv_batch_run(arr, len(items), _opts_ptr(opts), st)
+    return outs, list(st)
+
+
+class Plan:
+    """Host-side plan of a gate list (sv_plan_build); needs no GPU."""
+
+    def __init__(self, n: int, dtype, gates, opts=None):
+        self.gates = as_gates(gates)
+        h = _vp()
+        _check(_lib.sv_plan_build(n, DTYPES[dtype], self.gates.ctypes.data if len(self.gates) else None,
+                                  len(self.gates), _opts_ptr(opts), ctypes.byref(h)), "sv_plan_build")
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.sv_plan_free(self._h)
+            self._h = None
+
+    def summary(self) -> dict:
+        s = PlanSummary()
+        _check(_lib.sv_plan_summary_get(self._h, ctypes.byref(s)), "sv_plan_summary_get")
+        return {f: getattr(s, f) for f, _ in PlanSummary._fields_}
+
+    def block(self, b: int) -> dict:
+        kind, k, ng = _i32(), _i32(), _i32()
+        qs = (_i32 * 5)()
+        _check(_lib.sv_plan_block(self._h, b, ctypes.byref(kind), ctypes.byref(k), qs, ctypes.byref(ng),
+                                  None, 0, None, 0), "sv_plan_block")
+        ids = (_i32 * max(ng.value, 1))()
+        d = 1 << k.value
+        nm = d * d if kind.value == 0 else d
+        mat = (ctypes.c_double * (2 * nm))()
+        _check(_lib.sv_plan_block(self._h, b, None, None, None, None, ids, ng.value, mat, 2 * nm), "sv_plan_block")
+        m = np.frombuffer(mat, dtype=np.float64).copy().view(np.complex128)
+        return {"kind": kind.value, "k": k.value, "qubits": list(qs)[: k.value],
+                "gates": list(ids)[: ng.value], "mat": m.reshape(d, d) if kind.value == 0 else m}
+
+    def pass_info(self, i: int) -> dict:
+        mask, nb = _u64(), _i32()
+        _check(_lib.sv_plan_pass(self._h, i, ctypes.byref(mask), ctypes.byref(nb), None, 0), "sv_plan_pass")
+        ids = (_i32 * max(nb.value, 1))()
+        _check(_lib.sv_plan_pass(self._h, i, None, None, ids, nb.value), "sv_plan_pass")
+        return {"local_mask": mask.value, "blocks": list(ids)[: nb.value]}
+
+    def check(self) -> int:
+        return int(_lib.sv_plan_check(self._h, self.gates.ctypes.data if len(self.gates) else None,
+                                      len(self.gates)))

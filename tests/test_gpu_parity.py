@@ -1,0 +1,227 @@
+"""GPU parity: the sm_103a path (through the C-ABI) against the CPU oracle,
+element by element on the same seeded inputs.
+
+Tolerances: max |delta amplitude| <= 1e-12 for complex128 and <= 1e-5 for
+complex64; |sum p - 1| <= 1e-10 (complex128) and <= 1e-4 (complex64)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_11385_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = {"c128": 1e-12, "c64": 1e-5}
+NORM_TOL = {"c128": 1e-10, "c64": 1e-4}
+
+
+@pytest.fixture(scope="module")
+def sv():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2502_11385_gb300 import sv as _sv
+    return _sv
+
+
+def _random_circuit(n, count, seed, ops=range(14)):
+    rng = np.random.default_rng(seed)
+    ops = list(ops)
+    rows = []
+    for _ in range(count):
+        op = int(rng.choice(ops))
+        q0 = int(rng.integers(0, n))
+        q1 = -1
+        if op >= W.CX:
+            if n < 2:
+                continue
+            q1 = int(rng.choice([q for q in range(n) if q != q0]))
+        rows.append((op, q0, q1, *rng.uniform(-7, 7, 3)))
+    return W.gates(rows)
+
+
+def _run(sv, n, dtype, g, **opts):
+    with sv.State(n, dtype) as s:
+        s.apply_circuit(g, sv.run_opts(**opts) if opts else None)
+        return s.amplitudes().astype(np.complex128), s.probabilities(), s.norm(), s.stats()
+
+
+def _check(sv, n, dtype, g, ref=None, **opts):
+    if ref is None:
+        ref = oracle.run(n, g)
+    amp, p, nrm, st = _run(sv, n, dtype, g, **opts)
+    err = np.abs(amp - ref).max()
+    assert err <= TOL[dtype], (n, dtype, opts, err)
+    pref = oracle.probabilities(ref)
+    assert np.abs(p - pref).max() <= 4 * TOL[dtype]
+    assert abs(nrm - 1.0) <= NORM_TOL[dtype]
+    return st
+
+
+def test_brickwork12_unfused_c128(sv):
+    """12 qubits, brickwork depth 10, seed 1, complex128, no fusion."""
+    g = W.workload_brickwork12()
+    ref = oracle.run(12, g)
+    st = _check(sv, 12, "c128", g, ref, max_fuse_k=1)
+    assert st["n_blocks"] == 175 and st["n_passes"] == 1
+    _check(sv, 12, "c64", g, ref, max_fuse_k=1)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 12])
+def test_every_gate_on_every_operand(sv, n, dtype):
+    """Each gate type on every target (and every ordered control/target pair)
+    after a random preparation, unfused and fused."""
+    prep = _random_circuit(n, 3 * n, 7 + n, ops=[W.U3, W.CX] if n > 1 else [W.U3])
+    for op in range(14):
+        rows = []
+        for q0 in range(n):
+            if op >= W.CX:
+                rows += [(op, q0, q1, 0.37 + q0 - 0.11 * q1) for q1 in range(n) if q1 != q0]
+            else:
+                rows.append((op, q0, -1, 0.3 + 0.7 * q0, -1.1 + q0, 2.3 - q0))
+        if not rows:
+            continue
+        g = W.concat(prep, W.gates(rows))
+        ref = oracle.run(n, g)
+        _check(sv, n, dtype, g, ref, max_fuse_k=1)
+        _check(sv, n, dtype, g, ref, max_fuse_k=4)
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n,tile", [(10, 0), (16, 9), (18, 10), (20, 0)])
+def test_random_circuits_multi_pass(sv, n, tile, k, dtype):
+    g = _random_circuit(n, 120, 1000 * n + k)
+    st = _check(sv, n, dtype, g, max_fuse_k=k, tile_qubits=tile)
+    if tile and n > tile + 2:
+        assert st["n_passes"] > 1
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_high_qubits_and_ragged_tiles(sv, dtype):
+    # n just above the tile size, gates concentrated on the top qubits
+    n = 15
+    rows = []
+    for rep in range(4):
+        for q in range(n - 1, n - 6, -1):
+            rows.append((W.U3, q, -1, 0.2 * q + rep, 0.1 * rep, -0.3 * q))
+        rows += [(W.CX, n - 1, 0), (W.RZZ, 0, n - 1, 0.7), (W.SWAP, 1, n - 2), (W.CZ, n - 3, 2)]
+    g = W.gates(rows)
+    for tile in (0, 10, 11):
+        _check(sv, n, dtype, g, max_fuse_k=5, tile_qubits=tile)
+
+
+def test_ghz_closed_form_large(sv):
+    for n, dtype in ((26, "c128"), (27, "c64")):
+        with sv.State(n, dtype) as s:
+            s.apply_circuit(W.ghz_prefix(n))
+            p = s.probabilities()
+            assert abs(p[0] - 0.5) < NORM_TOL[dtype] and abs(p[-1] - 0.5) < NORM_TOL[dtype]
+            assert np.abs(p[1:-1]).max() < 1e-12
+            a = s.amplitudes()
+            assert abs(a[0] - 1 / math.sqrt(2)) <= TOL[dtype]
+
+
+def test_qft_of_basis_state(sv):
+    n, j = 16, 40503
+    g = W.qft_basis(n, j)
+    k = np.arange(1 << n)
+    ref = np.exp(2j * np.pi * j * k / (1 << n)) / math.sqrt(1 << n)
+    for dtype in ("c128", "c64"):
+        amp, _, _, _ = _run(sv, n, dtype, g)
+        assert np.abs(amp - ref).max() <= TOL[dtype]
+
+
+def test_marginals_and_norm_exactness(sv):
+    n = 14
+    g = W.concat(W.ghz_prefix(n), W.brickwork(n, 5, 3))
+    ref = oracle.run(n, g)
+    for dtype in ("c128", "c64"):
+        with sv.State(n, dtype) as s:
+            s.apply_circuit(g)
+            for mask in (0b1, 0b10000000000001, 0b11111000000000, (1 << n) - 1, 0b1010101):
+                m = s.marginal_probabilities(mask)
+                assert np.abs(m - oracle.marginal(ref, mask)).max() <= 4 * TOL[dtype] * (1 << (n // 2))
+            a, b = s.norm(), s.norm()
+            assert a == b                       # order-independent accumulation
+            amp = s.amplitudes().astype(np.complex128)
+            assert abs(a - math.fsum(np.abs(amp) ** 2)) < 1e-15
+
+
+def test_reset_basis_and_set_amplitudes(sv):
+    n = 9
+    with sv.State(n, "c128") as s:
+        s.reset(300)
+        a = s.amplitudes()
+        assert a[300] == 1 and np.count_nonzero(a) == 1
+        g = W.brickwork(n, 4, 5)
+        s.apply_circuit(g)
+        assert np.abs(s.amplitudes() - oracle.run(n, g, basis=300)).max() <= 1e-12
+        rng = np.random.default_rng(0)
+        v = rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n)
+        v /= np.linalg.norm(v)
+        s.set_amplitudes(v)
+        s.apply_circuit(g)
+        assert np.abs(s.amplitudes() - oracle.apply(n, v.copy(), g)).max() <= 1e-12
+
+
+def test_errors_leave_state_untouched(sv):
+    n = 6
+    with sv.State(n, "c64") as s:
+        s.apply_circuit(W.gates([(W.H, 0, -1)]))
+        before = s.amplitudes().copy()
+        for bad, code in [((W.CX, 2, 2), sv.SV_ERR_QUBIT), ((W.H, 6, -1), sv.SV_ERR_QUBIT),
+                          ((77, 0, -1), sv.SV_ERR_ARG)]:
+            with pytest.raises(sv.SvError) as e:
+                s.apply_circuit(W.gates([(W.X, 1, -1), bad]))
+            assert e.value.code == code
+        assert np.array_equal(s.amplitudes(), before)
+        s.apply_circuit(W.gates([]))
+        assert np.array_equal(s.amplitudes(), before)
+        with pytest.raises(sv.SvError) as e:
+            s.probabilities(np.empty(10))
+        assert e.value.code == sv.SV_ERR_SIZE
+    with pytest.raises(sv.SvError):
+        sv.State(0, "c64")
+    with pytest.raises(sv.SvError):
+        sv.State(35, "c128")
+
+
+def test_wrap_torch_tensor(sv):
+    import torch
+    n = 11
+    t = torch.zeros(1 << n, dtype=torch.complex128, device="cuda")
+    t[0] = 1
+    torch.cuda.synchronize()
+    s = sv.State.from_tensor(t, n, "c128", stream=torch.cuda.current_stream().cuda_stream)
+    g = W.brickwork(n, 5, 8)
+    s.apply_circuit(g)
+    torch.cuda.synchronize()
+    ref = oracle.run(n, g)
+    assert np.abs(t.cpu().numpy() - ref).max() <= 1e-12
+    p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    s.probabilities(p)
+    assert np.abs(p.cpu().numpy() - oracle.probabilities(ref)).max() <= 1e-12
+    s.close()
+
+
+def test_config2_30q_uudagger_is_ghz(sv):
+    """30 qubits, complex128: GHZ prefix + depth-20 brickwork (seed 2), then the
+    inverse brickwork; the result must be the GHZ closed form."""
+    n = 30
+    body = W.brickwork(n, 20, 2)
+    g = W.concat(W.ghz_prefix(n), body, W.inverse(body))
+    import torch
+    with sv.State(n, "c64") as s:
+        s.apply_circuit(g)
+        p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+        s.probabilities(p)
+        assert abs(p[0].item() - 0.5) < 1e-4 and abs(p[-1].item() - 0.5) < 1e-4
+        p[0] = 0
+        p[-1] = 0
+        assert p.max().item() < 1e-9
+        assert abs(s.norm() - 1) < 1e-4
