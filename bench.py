@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark of the statevector hot path on GB300.
+
+One step = the whole path over one circuit: validate + plan (fusion, tile
+passes) + initialise |0..0> + every tile pass + probabilities.  Workload: 30
+qubits, complex128 (16 GiB state), GHZ prefix then a seeded depth-20 random
+brickwork (920 gates), fusion up to 5 qubits (autotuned).
+
+Prints one JSON line.  `value` is statevector HBM GB/s: bytes the step's
+kernels must move (init write, 2 x state per tile pass, probability pass
+read + write) divided by the step time, with the state and output resident
+in HBM.  `e2e` is the same through host buffers (probabilities copied to
+pinned host memory inside the timed region).  `--impl reference` times the
+CPU oracle instead (a bounded sample of the same circuit on the host cores).
+With --gpus N > 1 (torchrun) every rank runs an independent replica.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_NOMINAL_TFLOPS = 1.25      # GB300 FP64 (CUDA cores), nominal
+FP32_FMA_PER_CLK_SM = 128       # FP32 lanes per SM
+SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--depth", type=int, default=20)
+    ap.add_argument("--dtype", default="c128", choices=["c128", "c64"])
+    ap.add_argument("--arith", type=int, default=0, help="0 auto, 1 native FP64, 2 double-float")
+    ap.add_argument("--fuse", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "device_types.hpp"):
+        with open(os.path.join(ROOT, "paper_2502_11385_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload_key, per_launch_scale):
+    """DRAM bytes per tile-pass launch from the committed ncu summary, or None
+    when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(workload_key)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e["dram_bytes_per_launch"] * per_launch_scale
+
+
+def cpu_baseline(n, gates, seconds, state_bytes_c128):
+    """The oracle (as it stands) on the host cores: applies the circuit's gates
+    one by one to a 2^n complex128 state until `seconds` have passed; each gate
+    is one read + write sweep of the state."""
+    import numpy as np
+    import oracle
+    avail = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    m = n
+    while m > 20 and (1 << m) * 16 * 1.5 > avail:
+        m -= 1
+    sample_gates = [g for g in gates if g["q0"] < m and (g["q1"] < m)]
+    psi = np.zeros(1 << m, dtype=np.complex128)
+    psi[0] = 1
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done < len(sample_gates):
+        oracle.apply(m, psi, sample_gates[done:done + 1])
+        done += 1
+    dt = time.perf_counter() - t0
+    gbs = done * 2 * (1 << m) * 16 / dt / 1e9
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {done} gates of the {n}-qubit circuit applied gate by gate to a {m}-qubit "
+                      f"complex128 state ({dt:.1f} s); GB/s = gates x 2 x state bytes / time"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2502_11385_gb300 import workloads as W
+    import oracle
+    gates = W.workload_ghz_brickwork(args.n, args.depth, 2)
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(args.n, gates, per_step, 0)
+        if i >= args.warmup:
+            vals.append(r["value"])
+        last = r
+    v = statistics.mean(vals) if vals else 0.0
+    out = {"impl": "reference", "metric": "statevector HBM GB/s vs peak at 30q c128", "value": round(v, 3),
+           "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.n}q GHZ + brickwork depth {args.depth} seed 2, complex128",
+                      "n_qubits": args.n},
+           "cpu_baseline": {"kind": "oracle", "cores": last["cores"], "sample": last["sample"], "value": round(v, 3),
+                            "unit": "GB/s"},
+           "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2502_11385_gb300 import sv, workloads as W
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    n, dt = args.n, args.dtype
+    gates = W.workload_ghz_brickwork(n, args.depth, 2)
+    ctype = torch.complex128 if dt == "c128" else torch.complex64
+    amp_bytes = 16 if dt == "c128" else 8
+    state_bytes = (1 << n) * amp_bytes
+    stream = torch.cuda.Stream()
+    buf = torch.empty(1 << n, dtype=ctype, device="cuda")
+    st = sv.State.from_tensor(buf, n, dt, stream=stream.cuda_stream)
+    probs = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    opts = sv.run_opts(max_fuse_k=args.fuse, tile_qubits=args.tile, arith=args.arith, timing=1)
+
+    stats_acc = []
+
+    def step(out):
+        st.reset(0)
+        st.apply_circuit(gates, opts)
+        stats_acc.append(st.stats())
+        st.probabilities(out)
+
+    for _ in range(args.warmup):
+        step(probs)
+    stats_acc.clear()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(probs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+
+    s0 = stats_acc[-1]
+    passes = s0["n_passes"]
+    step_bytes = state_bytes * (1 + 2 * passes + 1) + (1 << n) * 8
+    value = world * step_bytes / (ms / 1e3) / 1e9
+    launches_per_step = 1 + s0["n_launches"] + 1
+
+    # e2e: probabilities copied into pinned host memory every step
+    host_p = torch.empty(1 << n, dtype=torch.float64, pin_memory=True)
+    host_np = host_p.numpy()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        st.reset(0)
+        st.apply_circuit(gates, opts)
+        st.probabilities(host_np)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = t.item()
+    e2e_val = world * step_bytes / (e2e_ms / 1e3) / 1e9
+
+    peaks, peak_src = load_peaks()
+    kern_ms = statistics.mean(s["kernel_ms"] for s in stats_acc)
+    avg_launch_ms = kern_ms / max(1, s0["n_launches"])
+    flops = s0["flops"]
+    arith = s0["arith"]
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    hbm_achieved = 2 * state_bytes / (avg_launch_ms / 1e3) / 1e9
+    alu_achieved = flops / (kern_ms / 1e3) / 1e12
+    if dt == "c128" and arith == 1:
+        alu_peak, alu_name = FP64_NOMINAL_TFLOPS, "FP64 nominal 1.25 TFLOP/s"
+    else:
+        alu_peak = SMS * FP32_FMA_PER_CLK_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        alu_name = "FP32 152 SM x 128 lanes x 2 x max clock"
+    if alu_achieved / alu_peak > hbm_achieved / peaks["hbm_gbs"]:
+        roof = {"bound": "alu", "achieved": round(alu_achieved, 3), "peak": round(alu_peak, 2), "unit": "TFLOP/s",
+                "frac": round(alu_achieved / alu_peak, 4), "peak_source": alu_name}
+    else:
+        roof = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(hbm_achieved / peaks["hbm_gbs"], 4), "peak_source": f"{peak_src} hbm_gbs"}
+    wl_key = f"tile_pass_{n}q_{dt}"
+    roof["kernel"] = "k_tile_pass"
+    roof["traffic"] = ncu_traffic(wl_key, 1.0)
+    roof["hbm_gbs_per_launch"] = round(hbm_achieved, 1)
+    roof["frac_of_hbm_peak"] = round(hbm_achieved / peaks["hbm_gbs"], 4)
+
+    out = {"metric": "statevector HBM GB/s vs peak at 30q c128", "value": round(value, 2), "unit": "GB/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if dt == "c128" else "f32", "data": "synthetic",
+           "config": {"workload": f"{n}q GHZ + brickwork depth {args.depth} seed 2 ({len(gates)} gates), "
+                                  f"complex{128 if dt == 'c128' else 64}, fusion k<=5 autotuned",
+                      "n_qubits": n, "state_dtype": dt, "arith": {1: "native-fp64", 2: "df64"}.get(arith, "fp32"),
+                      "fuse_k": s0["fuse_k"], "tile_qubits": s0["tile_qubits"], "passes": passes,
+                      "blocks": s0["n_blocks"], "l2": f"state {state_bytes >> 30} GiB > L2, no flush needed",
+                      "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+           "frac_of_measured_hbm": round(value / peaks["hbm_gbs"], 4),
+           "frac_of_8tbs": round(value / 8000.0, 4),
+           "gate_equivalent_gbs": round(world * len(gates) * 2 * state_bytes / (ms / 1e3) / 1e9, 1),
+           "roofline": roof,
+           "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "ms_per_step": round(e2e_ms, 3),
+                   "h2d_bytes_per_step": int(s0["upload_bytes"]), "d2h_bytes_per_step": (1 << n) * 8},
+           "gpu_launches": launches_per_step * args.steps,
+           "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(n, gates, args.cpu_seconds, state_bytes)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    st.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

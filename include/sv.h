@@ -81,12 +81,16 @@ typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_NATIVE = 1, SV_ARITH_DF64 = 2 } sv_ar
  *   tile_qubits:  qubits per shared-memory tile (cache blocking, the
  *                 single-GPU counterpart of the chunk size nc, Sec. III-B).
  *   arith:        sv_arith for complex128 states.
- *   debug_checks: nonzero = check the plan's invariants before launching.   */
+ *   debug_checks: nonzero = check the plan's invariants before launching.
+ *   timing:       nonzero = record CUDA events around every kernel launch on
+ *                 the handle's stream and report the durations in
+ *                 sv_apply_stats (kernel_ms, max_kernel_ms).               */
 typedef struct {
     int32_t max_fuse_k;
     int32_t tile_qubits;
     int32_t arith;
     int32_t debug_checks;
+    int32_t timing;
 } sv_run_opts;
 
 typedef struct sv_state sv_state;
@@ -161,6 +165,9 @@ typedef struct {
     double  flops;           /* modelled arithmetic, real flops             */
     double  hbm_bytes;       /* passes x 2 x state bytes                    */
     double  plan_ms;         /* host planning time                          */
+    double  kernel_ms;       /* sum of kernel durations (opts->timing only) */
+    double  max_kernel_ms;   /* longest single launch (opts->timing only)   */
+    double  upload_bytes;    /* descriptors + coefficients copied host->device */
 } sv_apply_stats;
 int sv_last_stats(const sv_state* s, sv_apply_stats* out);
 

@@ -40,6 +40,7 @@ struct sv_state {
     size_t d_red_cap = 0;
     sv_apply_stats last{};
     bool failed = false;
+    std::vector<cudaEvent_t> events;  // timing events, reused across calls
 };
 
 struct sv_plan {
@@ -196,7 +197,7 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-int apply_plan(sv_state* s, const svp::Plan& P, int arith) {
+int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
     Lowered L;
     lower(P, L);
     const size_t ops_bytes = L.ops.size() * sizeof(DevOp);
@@ -221,15 +222,33 @@ int apply_plan(sv_state* s, const svp::Plan& P, int arith) {
         }
     }
     SV_TRY(cudaMemcpyAsync(s->d_ws, s->h_ws, total, cudaMemcpyHostToDevice, s->stream));
+    s->last.upload_bytes = (double)total;
     const auto* d_ops = (const DevOp*)s->d_ws;
     const void* d_coef = (const unsigned char*)s->d_ws + coef_off;
     int launches = 0;
+    if (timing) {
+        while (s->events.size() < L.passes.size() + 1) {
+            cudaEvent_t e;
+            SV_TRY(cudaEventCreate(&e));
+            s->events.push_back(e);
+        }
+        SV_TRY(cudaEventRecord(s->events[0], s->stream));
+    }
     for (const auto& dp : L.passes) {
         SV_TRY(svk::launch_tile_pass(s->dt, arith, s->amp, dp, d_ops, d_coef, s->stream, s->di));
         launches++;
+        if (timing) SV_TRY(cudaEventRecord(s->events[launches], s->stream));
     }
     SV_TRY(cudaStreamSynchronize(s->stream));
     s->last.n_launches = launches;
+    s->last.kernel_ms = 0;
+    s->last.max_kernel_ms = 0;
+    for (int i = 0; timing && i < launches; i++) {
+        float ms = 0;
+        SV_TRY(cudaEventElapsedTime(&ms, s->events[i], s->events[i + 1]));
+        s->last.kernel_ms += ms;
+        s->last.max_kernel_ms = std::max(s->last.max_kernel_ms, (double)ms);
+    }
     return SV_OK;
 }
 
@@ -311,6 +330,7 @@ void sv_destroy(sv_state* s) {
     if (s->d_ws) cudaFree(s->d_ws);
     if (s->h_ws) cudaFreeHost(s->h_ws);
     if (s->d_red) cudaFree(s->d_red);
+    for (cudaEvent_t e : s->events) cudaEventDestroy(e);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -339,7 +359,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     if (o && o->debug_checks && svp::check_plan(P, ng, g) != 0) return SV_ERR_STATE;
     const double t1 = now_ms();
     const int arith = resolve_arith(s->dt, o);
-    rc = apply_plan(s, P, arith);
+    rc = apply_plan(s, P, arith, o && o->timing);
     s->last.n_blocks = (int32_t)P.blocks.size();
     s->last.n_passes = (int32_t)P.passes.size();
     s->last.fuse_k = P.fuse_k;

@@ -34,13 +34,15 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 class RunOpts(ctypes.Structure):
     _fields_ = [("max_fuse_k", ctypes.c_int32), ("tile_qubits", ctypes.c_int32),
-                ("arith", ctypes.c_int32), ("debug_checks", ctypes.c_int32)]
+                ("arith", ctypes.c_int32), ("debug_checks", ctypes.c_int32), ("timing", ctypes.c_int32)]
 
 
 class ApplyStats(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
                 ("tile_qubits", ctypes.c_int32), ("arith", ctypes.c_int32), ("n_launches", ctypes.c_int32),
-                ("flops", ctypes.c_double), ("hbm_bytes", ctypes.c_double), ("plan_ms", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("hbm_bytes", ctypes.c_double), ("plan_ms", ctypes.c_double),
+                ("kernel_ms", ctypes.c_double), ("max_kernel_ms", ctypes.c_double),
+                ("upload_bytes", ctypes.c_double)]
 
 
 class BatchItem(ctypes.Structure):
@@ -119,8 +121,8 @@ def as_gates(gates) -> np.ndarray:
     return g
 
 
-def run_opts(max_fuse_k=0, tile_qubits=0, arith=ARITH_AUTO, debug_checks=0):
-    return RunOpts(max_fuse_k, tile_qubits, arith, debug_checks)
+def run_opts(max_fuse_k=0, tile_qubits=0, arith=ARITH_AUTO, debug_checks=0, timing=0):
+    return RunOpts(max_fuse_k, tile_qubits, arith, debug_checks, timing)
 
 
 def _opts_ptr(opts):
@@ -132,12 +134,23 @@ def _opts_ptr(opts):
 
 
 def _ptr_of(buf):
-    """(pointer, is_device) for a numpy array or a torch tensor."""
+    """(pointer, is_device, bytes) for a contiguous numpy array or torch tensor."""
     if isinstance(buf, np.ndarray):
-        return buf.ctypes.data, 0
+        if not buf.flags.c_contiguous:
+            raise ValueError("buffer must be C-contiguous")
+        return buf.ctypes.data, 0, buf.nbytes
     if hasattr(buf, "data_ptr"):
-        return buf.data_ptr(), 1 if buf.is_cuda else 0
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr(), 1 if buf.is_cuda else 0, buf.numel() * buf.element_size()
     raise TypeError(type(buf))
+
+
+def _f64_len(buf, nbytes):
+    itemsize = buf.itemsize if isinstance(buf, np.ndarray) else buf.element_size()
+    if itemsize != 8:
+        raise TypeError("probability buffers hold float64")
+    return nbytes // 8
 
 
 class State:
@@ -205,28 +218,31 @@ class State:
     def probabilities(self, out=None):
         if out is None:
             out = np.empty(self.dim, dtype=np.float64)
-        p, dev = _ptr_of(out)
-        _check(_lib.sv_probabilities(self._h, p, self.dim, dev), "sv_probabilities")
+        p, dev, nb = _ptr_of(out)
+        _check(_lib.sv_probabilities(self._h, p, _f64_len(out, nb), dev), "sv_probabilities")
         return out
 
     def marginal_probabilities(self, qubit_mask: int, out=None):
         nb = 1 << bin(qubit_mask).count("1")
         if out is None:
             out = np.empty(nb, dtype=np.float64)
-        p, dev = _ptr_of(out)
-        _check(_lib.sv_marginal_probabilities(self._h, qubit_mask, p, nb, dev), "sv_marginal_probabilities")
+        p, dev, nbytes = _ptr_of(out)
+        _check(_lib.sv_marginal_probabilities(self._h, qubit_mask, p, _f64_len(out, nbytes), dev),
+               "sv_marginal_probabilities")
         return out
 
     def amplitudes(self, out=None):
         if out is None:
             out = np.empty(self.dim, dtype=NP_DTYPE[self.dt])
-        p, dev = _ptr_of(out)
-        _check(_lib.sv_amplitudes(self._h, p, state_bytes(self.n, self.dt), dev), "sv_amplitudes")
+        p, dev, nb = _ptr_of(out)
+        _check(_lib.sv_amplitudes(self._h, p, nb, dev), "sv_amplitudes")
         return out
 
     def set_amplitudes(self, src):
-        p, dev = _ptr_of(src)
-        _check(_lib.sv_set_amplitudes(self._h, p, state_bytes(self.n, self.dt), dev), "sv_set_amplitudes")
+        if isinstance(src, np.ndarray):
+            src = np.ascontiguousarray(src, dtype=NP_DTYPE[self.dt])
+        p, dev, nb = _ptr_of(src)
+        _check(_lib.sv_set_amplitudes(self._h, p, nb, dev), "sv_set_amplitudes")
 
     def norm(self) -> float:
         v = ctypes.c_double()
@@ -253,7 +269,9 @@ def batch_run(items, opts=None):
         g = as_gates(gates)
         if out is None:
             out = np.empty(1 << n, dtype=np.float64)
-        p, dev = _ptr_of(out)
+        p, dev, nb = _ptr_of(out)
+        if nb != 8 << n:
+            raise ValueError("probs_out must hold 2^n float64")
         keep.append(g)
         outs.append(out)
         arr[i] = BatchItem(n, DTYPES[dtype], g.ctypes.data if len(g) else None, len(g), p, dev)
