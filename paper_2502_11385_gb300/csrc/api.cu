@@ -121,8 +121,9 @@ svp::Plan plan_for(int n, int dt, const sv_gate* g, size_t ng, const sv_run_opts
     m = std::min(m, c + 10);
     m = std::max(m, c + svp::kMaxFuse);
     svp::Machine mc;
-    const bool fp64 = dt == SV_C128 && resolve_arith(dt, o) == SV_ARITH_NATIVE;
-    return svp::make_plan(n, g, ng, k, m, c, amp_bytes(dt), fp64, mc);
+    int ak = svp::AK_FP32;
+    if (dt == SV_C128) ak = resolve_arith(dt, o) == SV_ARITH_DF64 ? svp::AK_DF64 : svp::AK_FP64;
+    return svp::make_plan(n, g, ng, k, m, c, amp_bytes(dt), ak, mc);
 }
 
 // Serialises a plan into descriptors (passes by value, ops and coefficients
@@ -213,6 +214,17 @@ int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
         for (size_t i = 0; i < L.coef.size(); i++) {
             c[2 * i] = (float)L.coef[i].real();
             c[2 * i + 1] = (float)L.coef[i].imag();
+        }
+    } else if (arith == SV_ARITH_DF64) {
+        // (hi, lo) float pairs: hi = float(x), lo = float(x - hi)
+        auto* c = (float*)(h + coef_off);
+        for (size_t i = 0; i < L.coef.size(); i++) {
+            const double re = L.coef[i].real(), im = L.coef[i].imag();
+            const float rh = (float)re, ih = (float)im;
+            c[4 * i] = rh;
+            c[4 * i + 1] = (float)(re - (double)rh);
+            c[4 * i + 2] = ih;
+            c[4 * i + 3] = (float)(im - (double)ih);
         }
     } else {
         auto* c = (double*)(h + coef_off);

@@ -212,6 +212,234 @@ __global__ void __launch_bounds__(kTileThreads) k_tile_pass(Cx<R>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// K5-df: tile pass for complex128 states with double-float arithmetic.
+//
+// GB300's FP64 units run about 70x slower than its FP32 units, so complex128
+// gates are computed on (hi, lo) float pairs instead (Dekker 1971): each
+// float64 amplitude component is split once per pass, when the tile is
+// loaded, into hi = its leading 24 significant bits and lo = the next 23
+// (47 bits, |x - hi - lo| <= 2^-47 |x|), with integer bit operations so the
+// FP64 pipe stays idle; block products use error-free TwoProd (FMA) and
+// TwoSum transforms (the compensated dot product of Ogita, Rump and Oishi
+// 2005, with double-float inputs); the tile is re-assembled into float64 on
+// store, again with integer operations.
+// ---------------------------------------------------------------------------
+struct alignas(16) DF4 {
+    float rh, rl, ih, il;  // re = rh + rl, im = ih + il
+};
+
+__device__ __forceinline__ void d2df(double x, float& h, float& l) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7ff);
+    if (e < 897) {  // |x| < 2^-126 (or zero): below float's normal range, dropped
+        h = 0.f;
+        l = 0.f;
+        return;
+    }
+    // amplitudes satisfy |x| <= 1 < 2^127, so e - 896 fits float's exponent field
+    h = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+    const unsigned r = (lo32 >> 6) & 0x7FFFFFu;  // next 23 mantissa bits, weight 2^(e-1069)
+    const int B = e - 919;                       // float exponent field with 2^(B-150) = 2^(e-1069)
+    if (B < 1 || r == 0u) {
+        l = 0.f;
+        return;
+    }
+    const unsigned one = sign | ((unsigned)B << 23);
+    l = __fadd_rn(__uint_as_float(one | r), -__uint_as_float(one));  // exact: (1 + r 2^-23) 2^(B-127) - 2^(B-127)
+}
+
+__device__ __forceinline__ double df2d(float h, float l) {
+    const float s = __fadd_rn(h, l);  // Fast2Sum: |l| <= ulp(s)/2 afterwards
+    l = __fadd_rn(l, -__fadd_rn(s, -h));
+    h = s;
+    const unsigned hb = __float_as_uint(h);
+    const unsigned eh = (hb >> 23) & 0xffu;
+    if (eh == 0u) return 0.0;  // zero or subnormal hi: below the amplitudes' range
+    const unsigned long long D = ((unsigned long long)(hb & 0x80000000u) << 32) |
+                                 ((unsigned long long)(eh + 896u) << 52) |
+                                 ((unsigned long long)(hb & 0x7FFFFFu) << 29);
+    const unsigned lb = __float_as_uint(l);
+    const unsigned el = (lb >> 23) & 0xffu;
+    if (el == 0u) return __longlong_as_double((long long)D);
+    // l in units of ulp_double(h) = 2^(eh - 179): k = ml * 2^(el - eh + 29), el <= eh - 24
+    const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
+    const int sh = (int)el - (int)eh + 29;
+    unsigned long long k = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> (-sh)) : 0ull);
+    unsigned long long mag = D & 0x7FFFFFFFFFFFFFFFull;
+    if ((lb ^ hb) & 0x80000000u) {
+        if ((hb & 0x7FFFFFu) == 0u) k <<= 1;  // hi is a power of two: the result lies in the lower binade
+        mag -= k;
+    } else {
+        mag += k;  // no carry out of the mantissa: |l| <= 2^28 ulp_double(h)
+    }
+    return __longlong_as_double((long long)((D & 0x8000000000000000ull) | mag));
+}
+
+// (sh, sl) += x * y for double-floats x = (xh, xl), y = (yh, yl): TwoProd of the
+// high parts, first-order cross terms, TwoSum into the running sum.  __fmul_rn
+// and __fadd_rn keep the compiler from contracting the transforms into FMAs.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float xh, float xl, float yh, float yl) {
+    const float ph = __fmul_rn(xh, yh);
+    const float pe = fmaf(xh, yh, -ph);
+    const float pl = fmaf(xh, yl, fmaf(xl, yh, pe));
+    const float s = __fadd_rn(sh, ph);
+    const float bb = __fadd_rn(s, -sh);
+    const float err = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bb)), __fadd_rn(ph, -bb));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, pl));
+}
+
+__device__ __forceinline__ void df_norm(float& h, float& l) {
+    const float s = __fadd_rn(h, l);
+    l = __fadd_rn(l, -__fadd_rn(s, -h));
+    h = s;
+}
+
+// out = sum_c M[c] * a[c] over complex double-floats
+template <int D>
+__device__ __forceinline__ DF4 df_dot(const DF4* __restrict__ Mrow, const DF4 (&a)[D]) {
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; c++) {
+        const DF4 u = Mrow[c];
+        df_mac(rh, rl, u.rh, u.rl, a[c].rh, a[c].rl);
+        df_mac(rh, rl, -u.ih, -u.il, a[c].ih, a[c].il);
+        df_mac(ih, il, u.rh, u.rl, a[c].ih, a[c].il);
+        df_mac(ih, il, u.ih, u.il, a[c].rh, a[c].rl);
+    }
+    df_norm(rh, rl);
+    df_norm(ih, il);
+    return DF4{rh, rl, ih, il};
+}
+
+template <int K>
+__device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, const DF4* __restrict__ M) {
+    constexpr int D = 1 << K;
+    int pos[K], pm[K];
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        pos[j] = op.pos[j];
+        pm[j] = 1 << pos[j];
+    }
+    const int ng = 1 << (m - K);
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        int base = g;
+#pragma unroll
+        for (int j = 0; j < K; j++) {
+            const int p = pos[j];
+            base = ((base >> p) << (p + 1)) | (base & ((1 << p) - 1));
+        }
+        DF4 a[D];
+#pragma unroll
+        for (int b = 0; b < D; b++) a[b] = sm[swz<double>(base | group_offset<K>(b, pm))];
+#pragma unroll(K <= 1 ? D : 1)
+        for (int r = 0; r < D; r++) sm[swz<double>(base | group_offset<K>(r, pm))] = df_dot<D>(M + r * D, a);
+    }
+}
+
+__device__ __forceinline__ void op_diag_df(DF4* sm, int m, const DevOp& op, const DF4* __restrict__ M,
+                                           uint64_t tile_base) {
+    int cidx = 0, lp[5], lb[5], nl = 0;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        if (j < op.k) {
+            if (op.pos[j] < 0) {
+                cidx |= (int)((tile_base >> op.qbit[j]) & 1) << j;
+            } else {
+                lp[nl] = op.pos[j];
+                lb[nl] = j;
+                nl++;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 5; j++)
+        if (j >= nl) { lp[j] = 0; lb[j] = 31; }
+    const int N = 1 << m;
+    const bool sign_only = op.flags & OPF_SIGN_ONLY;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        int idx = cidx;
+#pragma unroll
+        for (int j = 0; j < 5; j++) idx |= (lb[j] < 31) ? (((i >> lp[j]) & 1) << lb[j]) : 0;
+        const DF4 u = M[idx];
+        const int s = swz<double>(i);
+        const DF4 a = sm[s];
+        if (sign_only) {
+            if (u.rh < 0.f) sm[s] = DF4{-a.rh, -a.rl, -a.ih, -a.il};
+        } else {
+            float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+            df_mac(rh, rl, u.rh, u.rl, a.rh, a.rl);
+            df_mac(rh, rl, -u.ih, -u.il, a.ih, a.il);
+            df_mac(ih, il, u.rh, u.rl, a.ih, a.il);
+            df_mac(ih, il, u.ih, u.il, a.rh, a.rl);
+            df_norm(rh, rl);
+            df_norm(ih, il);
+            sm[s] = DF4{rh, rl, ih, il};
+        }
+    }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(kTileThreads) k_tile_pass_df(Cx<double>* __restrict__ st, const DevPass P,
+                                                               const DevOp* __restrict__ ops,
+                                                               const DF4* __restrict__ coef) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    DF4* sm = reinterpret_cast<DF4*>(smraw);
+    __shared__ uint64_t dep[2][32];
+    const int m = P.m, c = P.c, hb = m - c;
+    if (threadIdx.x < 64) {
+        const int w = threadIdx.x >> 5, v = threadIdx.x & 31;
+        uint64_t d = 0;
+        for (int b = 0; b < 5; b++) {
+            const int bit = w * 5 + b;
+            if (bit < hb && ((v >> b) & 1)) d |= 1ull << P.L[c + bit];
+        }
+        dep[w][v] = d;
+    }
+    __syncthreads();
+    const int N = 1 << m;
+    const int cmask = (1 << c) - 1;
+    for (uint64_t t = blockIdx.x; t < P.tile_count; t += gridDim.x) {
+        uint64_t base = 0;
+        for (int b = 0; b < P.n - m; b++)
+            if ((t >> b) & 1) base |= 1ull << P.NL[b];
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            const int r = j >> c;
+            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+            const Cx<double> a = st[gidx];
+            DF4 v;
+            d2df(a.re, v.rh, v.rl);
+            d2df(a.im, v.ih, v.il);
+            sm[swz<double>(j)] = v;
+        }
+        __syncthreads();
+        for (int o = 0; o < P.n_ops; o++) {
+            const DevOp op = ops[P.op0 + o];
+            const DF4* M = coef + op.coeff;
+            if (op.kind == OP_DIAG) {
+                op_diag_df(sm, m, op, M, base);
+            } else {
+                if (op.k == 1) op_dense_df<1>(sm, m, op, M);
+                else if (op.k == 2) op_dense_df<(KMAX >= 2 ? 2 : 1)>(sm, m, op, M);
+                else if (op.k == 3) op_dense_df<(KMAX >= 3 ? 3 : 1)>(sm, m, op, M);
+                else if (op.k == 4) op_dense_df<(KMAX >= 4 ? 4 : 1)>(sm, m, op, M);
+                else op_dense_df<(KMAX >= 5 ? 5 : 1)>(sm, m, op, M);
+            }
+            __syncthreads();
+        }
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            const int r = j >> c;
+            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+            const DF4 v = sm[swz<double>(j)];
+            st[gidx] = Cx<double>{df2d(v.rh, v.rl), df2d(v.ih, v.il)};
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // K7: probabilities, exact norm, marginals.
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -401,9 +629,38 @@ static cudaError_t tile_pass_k(int kmax, void* amp, const DevPass& p, const DevO
     }
 }
 
+template <int KMAX>
+static cudaError_t tile_pass_df_impl(void* amp, const DevPass& p, const DevOp* d_ops, const void* d_coef,
+                                     cudaStream_t s, const DevInfo& di) {
+    const size_t smem = ((size_t)1 << p.m) * sizeof(DF4);
+    static int configured_dev = -1;
+    if (configured_dev != di.device) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_pass_df<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(di.smem_optin - 2048));
+        if (e != cudaSuccess) return e;
+        configured_dev = di.device;
+    }
+    int per_sm = 1;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass_df<KMAX>, kTileThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    uint64_t grid = (uint64_t)di.sms * per_sm;
+    if (grid > p.tile_count) grid = p.tile_count;
+    k_tile_pass_df<KMAX><<<(unsigned)grid, kTileThreads, smem, s>>>((Cx<double>*)amp, p, d_ops, (const DF4*)d_coef);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tile_pass(int dt, int arith, void* amp, const DevPass& p, const DevOp* d_ops,
                              const void* d_coef, cudaStream_t s, const DevInfo& di) {
-    (void)arith;
+    if (dt == SV_C128 && arith == SV_ARITH_DF64) {
+        switch (p.kmax) {
+            case 1: return tile_pass_df_impl<1>(amp, p, d_ops, d_coef, s, di);
+            case 2: return tile_pass_df_impl<2>(amp, p, d_ops, d_coef, s, di);
+            case 3: return tile_pass_df_impl<3>(amp, p, d_ops, d_coef, s, di);
+            case 4: return tile_pass_df_impl<4>(amp, p, d_ops, d_coef, s, di);
+            default: return tile_pass_df_impl<5>(amp, p, d_ops, d_coef, s, di);
+        }
+    }
     if (dt == SV_C64) return tile_pass_k<float>(p.kmax, amp, p, d_ops, d_coef, s, di);
     return tile_pass_k<double>(p.kmax, amp, p, d_ops, d_coef, s, di);
 }

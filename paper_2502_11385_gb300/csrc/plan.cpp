@@ -220,23 +220,38 @@ std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, 
 }
 
 static double block_flops(const Block& b, double dim) {
-    // real flops (FMA = 2) applied to the whole 2^n state
+    // real flops (FMA = 2) of the block applied to the whole 2^n state
     if (b.kind == BK_DIAG) return b.sign_only ? 0.0 : 6.0 * dim;
     return 8.0 * (double)(1 << b.k) * dim;
 }
 
-double model_cost(const Plan& p, int amp_bytes, bool fp64_alu, const Machine& mc, double* flops) {
+// ALU lane instructions per amplitude for one block.
+static double block_instr(const Block& b, int arith) {
+    const double D = (double)(1 << b.k);
+    if (b.kind == BK_DIAG) {
+        if (b.sign_only) return 1.0;
+        return arith == AK_DF64 ? 44.0 : 4.0;
+    }
+    // complex multiply-add: 4 real FMAs; double-float: 4 x (TwoProd + cross
+    // terms + TwoSum) = 44 FP32 instructions
+    return (arith == AK_DF64 ? 44.0 : 4.0) * D;
+}
+
+double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops) {
     const double dim = std::ldexp(1.0, p.n);
     const double state = dim * amp_bytes;
+    const double rate = arith == AK_FP64 ? mc.fp64_ips : mc.fp32_ips;
     double total = 0, fl_all = 0;
     for (const auto& ps : p.passes) {
-        double fl = 0, smem = 0;
+        double fl = 0, instr = 0, smem = 0;
         for (int bi : ps.blocks) {
             fl += block_flops(p.blocks[bi], dim);
+            instr += block_instr(p.blocks[bi], arith) * dim;
             smem += 2.0 * state;
         }
+        if (arith == AK_DF64) instr += 60.0 * dim;  // float64 <-> double-float conversions per pass
         fl_all += fl;
-        const double alu = fl / 2.0 / (fp64_alu ? mc.fp64_fma_ps : mc.fp32_fma_ps);
+        const double alu = instr / rate;
         const double hbm = 2.0 * state / mc.hbm_Bps;
         const double sm = smem / mc.smem_Bps;
         total += std::max(std::max(alu, hbm), sm) + mc.launch_s;
@@ -246,7 +261,7 @@ double model_cost(const Plan& p, int amp_bytes, bool fp64_alu, const Machine& mc
 }
 
 Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int coalesce,
-               int amp_bytes, bool fp64_alu, const Machine& mc) {
+               int amp_bytes, int arith, const Machine& mc) {
     Plan best;
     best.model_s = 1e300;
     int k_lo = fuse_k > 0 ? fuse_k : 1, k_hi = fuse_k > 0 ? fuse_k : kMaxFuse;
@@ -267,13 +282,13 @@ Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int c
         }
         p.passes = schedule(n, p.blocks, p.tile_m, p.coalesce);
         double fl = 0;
-        p.model_s = model_cost(p, amp_bytes, fp64_alu, mc, &fl);
+        p.model_s = model_cost(p, amp_bytes, arith, mc, &fl);
         p.flops = fl;
         if (p.model_s < best.model_s) best = std::move(p);
     }
     finalize(best.blocks, g);
     double fl = 0;
-    best.model_s = model_cost(best, amp_bytes, fp64_alu, mc, &fl);
+    best.model_s = model_cost(best, amp_bytes, arith, mc, &fl);
     best.flops = fl;
     return best;
 }

@@ -57,10 +57,14 @@ struct Plan {
     double model_s = 0;    // modelled time
 };
 
-struct Machine {           // throughput model used by the autotuner
+// Arithmetic of the tile kernels: float32 (complex64), native float64, or
+// double-float pairs on the FP32 units (complex128).
+enum ArithKind { AK_FP32 = 0, AK_FP64 = 1, AK_DF64 = 2 };
+
+struct Machine {           // throughput model used by the autotuner (measured on GB300)
     double hbm_Bps = 6.6e12;
-    double fp32_fma_ps = 3.2e13;
-    double fp64_fma_ps = 4.6e11;
+    double fp32_ips = 3.2e13;   // FP32 lane instructions per second (FFMA / FADD / FMUL)
+    double fp64_ips = 4.6e11;   // FP64 lane instructions per second
     double smem_Bps = 3.5e13;
     double launch_s = 4e-6;
 };
@@ -77,12 +81,13 @@ void finalize(std::vector<Block>& blocks, const sv_gate* g);
 // qubits are always local (contiguous runs for coalesced loads).
 std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, int coalesce);
 
-// Modelled cost of a plan (seconds) for a state of `amp_bytes` per amplitude.
-double model_cost(const Plan& p, int amp_bytes, bool fp64_alu, const Machine& mc, double* flops);
+// Modelled cost of a plan (seconds) for a state of `amp_bytes` per amplitude;
+// *flops receives the real flops of the block products (FMA = 2).
+double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops);
 
 // Full planning with optional autotuning over fuse_k (0 = auto).
 Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int coalesce,
-               int amp_bytes, bool fp64_alu, const Machine& mc);
+               int amp_bytes, int arith, const Machine& mc);
 
 // Checks plan invariants: every gate exactly once, per-qubit order kept,
 // block sizes, locality of dense blocks.  Returns 0 when valid.

@@ -225,3 +225,61 @@ def test_config2_30q_uudagger_is_ghz(sv):
         p[-1] = 0
         assert p.max().item() < 1e-9
         assert abs(s.norm() - 1) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# complex128 with double-float arithmetic on the FP32 units (SV_ARITH_DF64)
+# ---------------------------------------------------------------------------
+def test_df64_brickwork12(sv):
+    g = W.workload_brickwork12()
+    ref = oracle.run(12, g)
+    _check(sv, 12, "c128", g, ref, max_fuse_k=1, arith=sv.ARITH_DF64)
+    st = _check(sv, 12, "c128", g, ref, arith=sv.ARITH_DF64)
+    assert st["arith"] == sv.ARITH_DF64
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n,tile", [(10, 0), (16, 9), (20, 0)])
+def test_df64_random_circuits(sv, n, tile, k):
+    g = _random_circuit(n, 120, 7000 * n + k)
+    _check(sv, n, "c128", g, max_fuse_k=k, tile_qubits=tile, arith=sv.ARITH_DF64)
+
+
+@pytest.mark.parametrize("n", [3, 8, 12])
+def test_df64_every_gate_on_every_operand(sv, n):
+    prep = _random_circuit(n, 3 * n, 17 + n, ops=[W.U3, W.CX])
+    rows = []
+    for op in range(14):
+        for q0 in range(n):
+            if op >= W.CX:
+                rows += [(op, q0, q1, 0.37 + q0 - 0.11 * q1) for q1 in range(n) if q1 != q0]
+            else:
+                rows.append((op, q0, -1, 0.3 + 0.7 * q0, -1.1 + q0, 2.3 - q0))
+    g = W.concat(prep, W.gates(rows))
+    ref = oracle.run(n, g)
+    for k in (1, 3, 5):
+        _check(sv, n, "c128", g, ref, max_fuse_k=k, arith=sv.ARITH_DF64)
+
+
+def test_df64_conversion_roundtrip(sv):
+    """float64 -> (hi, lo) float pair -> float64 keeps 47 significant bits
+    (components >= 2^-100 in magnitude) across powers of two, signs and
+    magnitudes from 1 down to 1e-30; components below 2^-126 flush to zero."""
+    n = 12
+    rng = np.random.default_rng(5)
+    mag = 10.0 ** rng.uniform(-30, 0, size=(1 << n, 2))
+    sgn = rng.choice([-1.0, 1.0], size=(1 << n, 2))
+    v = mag * sgn
+    v[:64, 0] = 2.0 ** -np.arange(64)                       # powers of two
+    v[64:128, 1] = -(2.0 ** -np.arange(64)) * (1 + 2.0 ** -30)
+    v[128:136] = 1e-40                                      # below float's range
+    a = v[:, 0] + 1j * v[:, 1]
+    with sv.State(n, "c128") as s:
+        s.set_amplitudes(a)
+        s.apply_circuit(W.gates([(W.X, 0, -1), (W.X, 0, -1)]), sv.run_opts(max_fuse_k=1, arith=sv.ARITH_DF64))
+        out = s.amplitudes()
+    for got, want in ((out.real, v[:, 0]), (out.imag, v[:, 1])):
+        big = np.abs(want) >= 2.0 ** -100
+        rel = np.abs(got[big] - want[big]) / np.abs(want[big])
+        assert rel.max() <= 2.0 ** -46, rel.max()
+        assert np.all(got[np.abs(want) < 2.0 ** -126] == 0)
