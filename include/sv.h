@@ -171,11 +171,18 @@ typedef struct {
 } sv_apply_stats;
 int sv_last_stats(const sv_state* s, sv_apply_stats* out);
 
-/* Batched form: simulates every item from |0...0> (each its own width and
- * dtype) and writes its full probability vector (2^n float64) to probs_out.
- * Items are grouped by plan shape and run as multi-state launches captured
- * in one CUDA graph; states stay resident in a pooled device arena.
- * item_status[i] receives each item's sv_status (may be NULL). */
+/* Batched form -- the CutQC Evaluator's subcircuit instances (Sec. IV-A,
+ * "Evaluator"; three measurement and four initialisation variants per cut,
+ * Fig. 1), run together instead of by a pool of worker processes (Listing 4).
+ * Every item is simulated from |0...0> (each its own width and dtype) and its
+ * full probability vector (2^n float64) is written to probs_out (device or
+ * host memory, kept valid by the caller until the batch is destroyed).  The
+ * items' states live in one pooled device arena; each item is planned on its
+ * own (its result does not depend on the other items), and pass i of every
+ * item runs in one multi-state tile-pass launch.  The whole sequence (init,
+ * passes, probabilities) is captured once in a CUDA graph that
+ * sv_batch_execute replays.  item_status[i] receives each item's sv_status
+ * (may be NULL); invalid items are skipped, the others still run. */
 typedef struct {
     int32_t n_qubits;
     int32_t dt;
@@ -186,6 +193,24 @@ typedef struct {
 } sv_batch_item;
 int sv_batch_run(const sv_batch_item* items, size_t n_items,
                  const sv_run_opts* opts, int* item_status);
+
+/* The same in three steps, for replaying one batch many times: create (plan,
+ * allocate, upload, capture the graph), execute (replay and wait; copies
+ * host-side outputs), destroy.  sv_batch_create returns SV_ERR_OOM when the
+ * arena does not fit in free device memory. */
+typedef struct sv_batch sv_batch;
+int sv_batch_create(const sv_batch_item* items, size_t n_items,
+                    const sv_run_opts* opts, int* item_status, sv_batch** out);
+int sv_batch_execute(sv_batch* b);
+void sv_batch_destroy(sv_batch* b);
+
+/* Counts of a batch: launches in its graph, device bytes it holds, and the
+ * duration of the last sv_batch_execute measured with CUDA events. */
+typedef struct {
+    int32_t n_items, n_launches;
+    double arena_bytes, last_ms;
+} sv_batch_info;
+int sv_batch_stats(const sv_batch* b, sv_batch_info* out);
 
 /* Static description of a status code. */
 const char* sv_status_str(int status);

@@ -198,28 +198,21 @@ double now_ms() {
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
-    Lowered L;
-    lower(P, L);
-    const size_t ops_bytes = L.ops.size() * sizeof(DevOp);
-    const size_t esz = amp_bytes(s->dt);
-    const size_t coef_off = (ops_bytes + 255) & ~(size_t)255;
-    const size_t total = coef_off + L.coef.size() * esz + 256;
-    SV_TRY(ensure(&s->d_ws, &s->d_ws_cap, total, false));
-    SV_TRY(ensure(&s->h_ws, &s->h_ws_cap, total, true));
-    auto* h = (unsigned char*)s->h_ws;
-    if (ops_bytes) std::memcpy(h, L.ops.data(), ops_bytes);
-    if (s->dt == SV_C64) {
-        auto* c = (float*)(h + coef_off);
-        for (size_t i = 0; i < L.coef.size(); i++) {
-            c[2 * i] = (float)L.coef[i].real();
-            c[2 * i + 1] = (float)L.coef[i].imag();
+// Writes block coefficients in the kernel's format: complex64 -> float pairs,
+// complex128 native -> double pairs, complex128 df64 -> (hi, lo) float pairs.
+size_t coef_elem_bytes(int dt) { return dt == SV_C64 ? 8 : 16; }
+
+void write_coefs(const std::vector<svp::cd>& coef, int dt, int arith, unsigned char* dst) {
+    if (dt == SV_C64) {
+        auto* c = (float*)dst;
+        for (size_t i = 0; i < coef.size(); i++) {
+            c[2 * i] = (float)coef[i].real();
+            c[2 * i + 1] = (float)coef[i].imag();
         }
     } else if (arith == SV_ARITH_DF64) {
-        // (hi, lo) float pairs: hi = float(x), lo = float(x - hi)
-        auto* c = (float*)(h + coef_off);
-        for (size_t i = 0; i < L.coef.size(); i++) {
-            const double re = L.coef[i].real(), im = L.coef[i].imag();
+        auto* c = (float*)dst;  // hi = float(x), lo = float(x - hi)
+        for (size_t i = 0; i < coef.size(); i++) {
+            const double re = coef[i].real(), im = coef[i].imag();
             const float rh = (float)re, ih = (float)im;
             c[4 * i] = rh;
             c[4 * i + 1] = (float)(re - (double)rh);
@@ -227,16 +220,39 @@ int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
             c[4 * i + 3] = (float)(im - (double)ih);
         }
     } else {
-        auto* c = (double*)(h + coef_off);
-        for (size_t i = 0; i < L.coef.size(); i++) {
-            c[2 * i] = L.coef[i].real();
-            c[2 * i + 1] = L.coef[i].imag();
+        auto* c = (double*)dst;
+        for (size_t i = 0; i < coef.size(); i++) {
+            c[2 * i] = coef[i].real();
+            c[2 * i + 1] = coef[i].imag();
         }
+    }
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
+    Lowered L;
+    lower(P, L);
+    const size_t ops_bytes = L.ops.size() * sizeof(DevOp);
+    const size_t coef_off = align256(ops_bytes);
+    const size_t ent_off = align256(coef_off + L.coef.size() * coef_elem_bytes(s->dt));
+    const size_t total = ent_off + L.passes.size() * sizeof(svk::BatchEntry);
+    SV_TRY(ensure(&s->d_ws, &s->d_ws_cap, total, false));
+    SV_TRY(ensure(&s->h_ws, &s->h_ws_cap, total, true));
+    auto* h = (unsigned char*)s->h_ws;
+    if (ops_bytes) std::memcpy(h, L.ops.data(), ops_bytes);
+    write_coefs(L.coef, s->dt, arith, h + coef_off);
+    auto* ent = (svk::BatchEntry*)(h + ent_off);
+    for (size_t i = 0; i < L.passes.size(); i++) {
+        ent[i].state = (uint64_t)(uintptr_t)s->amp;
+        ent[i].tile_begin = 0;
+        ent[i].p = L.passes[i];
     }
     SV_TRY(cudaMemcpyAsync(s->d_ws, s->h_ws, total, cudaMemcpyHostToDevice, s->stream));
     s->last.upload_bytes = (double)total;
     const auto* d_ops = (const DevOp*)s->d_ws;
     const void* d_coef = (const unsigned char*)s->d_ws + coef_off;
+    const auto* d_ent = (const svk::BatchEntry*)((const unsigned char*)s->d_ws + ent_off);
     int launches = 0;
     if (timing) {
         while (s->events.size() < L.passes.size() + 1) {
@@ -246,8 +262,10 @@ int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
         }
         SV_TRY(cudaEventRecord(s->events[0], s->stream));
     }
-    for (const auto& dp : L.passes) {
-        SV_TRY(svk::launch_tile_pass(s->dt, arith, s->amp, dp, d_ops, d_coef, s->stream, s->di));
+    for (size_t i = 0; i < L.passes.size(); i++) {
+        const DevPass& dp = L.passes[i];
+        SV_TRY(svk::launch_tile_pass(s->dt, arith, d_ent + i, 1, dp.tile_count, dp.m, dp.kmax, d_ops, d_coef,
+                                     s->stream, s->di));
         launches++;
         if (timing) SV_TRY(cudaEventRecord(s->events[launches], s->stream));
     }
@@ -460,20 +478,285 @@ int sv_norm(sv_state* s, double* out) {
     return SV_OK;
 }
 
-int sv_batch_run(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, int* item_status) {
-    if (n_items && !items) return SV_ERR_ARG;
-    int worst = SV_OK;
+}  // extern "C"
+
+struct sv_batch {
+    svk::DevInfo di;
+    cudaStream_t stream = nullptr;
+    void* arena = nullptr;      // states, device-side probabilities, descriptors
+    size_t arena_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int n_items = 0, n_launches = 0;
+    double last_ms = 0;
+    struct HostCopy {
+        double* dst;
+        size_t off, bytes;
+    };
+    std::vector<HostCopy> host_copies;
+};
+
+namespace {
+
+struct BatchItemPlan {
+    int idx, n, dt, arith;
+    svp::Plan plan;
+    Lowered low;
+    size_t state_off = 0, probs_off = 0;  // in the arena
+    bool host_out = false;
+};
+
+void batch_free(sv_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->arena) cudaFree(b->arena);
+    for (auto& e : b->ev)
+        if (e) cudaEventDestroy(e);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sv_batch_create(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, int* item_status,
+                    sv_batch** out) {
+    if (!out || (n_items && !items)) return SV_ERR_ARG;
+    sv_batch* b = new (std::nothrow) sv_batch();
+    if (!b) return SV_ERR_OOM;
+    sv_state* s = nullptr;  // for SV_TRY
+    auto fail = [&](int rc) {
+        batch_free(b);
+        return rc;
+    };
+    if (device_info(&b->di) != cudaSuccess) return fail(SV_ERR_CUDA);
+    // plan every item on its own
+    std::vector<BatchItemPlan> P;
+    P.reserve(n_items);
     for (size_t i = 0; i < n_items; i++) {
         const sv_batch_item& it = items[i];
-        sv_state* s = nullptr;
-        int rc = sv_create(it.n_qubits, it.dt, &s);
-        if (rc == SV_OK) rc = sv_apply_circuit(s, it.gates, it.n_gates, opts);
-        if (rc == SV_OK) rc = sv_probabilities(s, it.probs_out, (size_t)1 << it.n_qubits, it.probs_on_device);
-        if (s) sv_destroy(s);
+        int rc = SV_OK;
+        if (it.n_qubits < 1 || it.n_qubits > svp::kMaxQubits || !dt_ok(it.dt) || !it.probs_out) rc = SV_ERR_ARG;
+        if (rc == SV_OK) rc = svp::validate(it.n_qubits, it.gates, it.n_gates);
         if (item_status) item_status[i] = rc;
-        if (rc != SV_OK && worst == SV_OK) worst = rc;
+        if (rc != SV_OK) continue;
+        BatchItemPlan bp;
+        bp.idx = (int)i;
+        bp.n = it.n_qubits;
+        bp.dt = it.dt;
+        bp.arith = resolve_arith(it.dt, opts);
+        bp.plan = plan_for(it.n_qubits, it.dt, it.gates, it.n_gates, opts, max_tile(it.dt, b->di));
+        lower(bp.plan, bp.low);
+        bp.host_out = !it.probs_on_device;
+        P.push_back(std::move(bp));
     }
-    return worst;
+    b->n_items = (int)P.size();
+    // arena layout: states | device-side probabilities (host outputs) | ops | coefs | entries
+    size_t off = 0;
+    for (auto& bp : P) {
+        bp.state_off = off;
+        off += align256(sv_state_bytes(bp.n, bp.dt));
+    }
+    for (auto& bp : P) {
+        if (!bp.host_out) continue;
+        bp.probs_off = off;
+        off += align256(((size_t)8) << bp.n);
+    }
+    // group by kernel mode (dtype, arithmetic)
+    auto mode_of = [](const BatchItemPlan& bp) { return bp.dt == SV_C64 ? 0 : (bp.arith == SV_ARITH_DF64 ? 2 : 1); };
+    std::vector<DevOp> ops;
+    std::vector<unsigned char> coefs;  // per-mode coefficient blobs, concatenated
+    struct Launch {
+        int mode, dt, arith, n_ent, max_m, kmax;
+        size_t ent_index;
+        uint64_t tiles;
+    };
+    std::vector<Launch> launches;
+    std::vector<svk::BatchEntry> entries;
+    std::vector<svk::StateEntry> sentries;
+    struct SLaunch {
+        int dt;
+        size_t first;
+        int count;
+        uint64_t amps;
+    };
+    std::vector<SLaunch> slaunch;
+    std::vector<size_t> coef_base(P.size(), 0), op_base(P.size(), 0);
+    for (size_t i = 0; i < P.size(); i++) {
+        auto& bp = P[i];
+        op_base[i] = ops.size();
+        for (auto op : bp.low.ops) ops.push_back(op);
+        // coefficient offsets are in elements; keep each item's blob aligned to its element size
+        const size_t esz = coef_elem_bytes(bp.dt);
+        size_t cb = (coefs.size() + esz - 1) / esz * esz;
+        coefs.resize(cb + bp.low.coef.size() * esz);
+        write_coefs(bp.low.coef, bp.dt, bp.arith, coefs.data() + cb);
+        coef_base[i] = cb;
+    }
+    const size_t ops_off = off;
+    off += align256(ops.size() * sizeof(DevOp) + 16);
+    const size_t coef_off = off;
+    off += align256(coefs.size() + 16);
+    // multi-state launches per (mode, pass index); the op/coef offsets inside each
+    // entry's pass point at the item's ops; coefficient offsets are rebased below
+    for (int mode = 0; mode < 3; mode++) {
+        size_t max_passes = 0;
+        std::vector<size_t> members;
+        for (size_t i = 0; i < P.size(); i++)
+            if (mode_of(P[i]) == mode) {
+                members.push_back(i);
+                max_passes = std::max(max_passes, P[i].low.passes.size());
+            }
+        if (members.empty()) continue;
+        SLaunch sl{P[members[0]].dt, sentries.size(), 0, 0};
+        for (size_t i : members) {
+            svk::StateEntry se{};
+            se.n = P[i].n;
+            sentries.push_back(se);  // addresses filled once the arena exists
+            sl.count++;
+            sl.amps += 1ull << P[i].n;
+        }
+        slaunch.push_back(sl);
+        for (size_t p = 0; p < max_passes; p++) {
+            Launch L{mode, P[members[0]].dt, P[members[0]].arith, 0, 1, 1, entries.size(), 0};
+            for (size_t i : members) {
+                if (p >= P[i].low.passes.size()) continue;
+                svk::BatchEntry e{};
+                e.tile_begin = L.tiles;
+                e.p = P[i].low.passes[p];
+                e.p.op0 += (int32_t)op_base[i];
+                e.state = (uint64_t)i;  // patched to an address below
+                entries.push_back(e);
+                L.n_ent++;
+                L.tiles += e.p.tile_count;
+                L.max_m = std::max(L.max_m, (int)e.p.m);
+                L.kmax = std::max(L.kmax, (int)e.p.kmax);
+            }
+            launches.push_back(L);
+        }
+    }
+    // rebase each op's coefficient offset: element offset inside its item's blob
+    for (size_t i = 0; i < P.size(); i++) {
+        const size_t esz = coef_elem_bytes(P[i].dt);
+        for (size_t o = 0; o < P[i].low.ops.size(); o++) ops[op_base[i] + o].coeff += (int32_t)(coef_base[i] / esz);
+    }
+    const size_t ent_off = off;
+    off += align256(entries.size() * sizeof(svk::BatchEntry) + 16);
+    const size_t sent_off = off;
+    off += align256(sentries.size() * sizeof(svk::StateEntry) + 16);
+    b->arena_bytes = off;
+    size_t fr = 0, to = 0;
+    if (cudaMemGetInfo(&fr, &to) == cudaSuccess && off > fr) return fail(SV_ERR_OOM);
+    cudaError_t e = cudaMalloc(&b->arena, off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA);
+    }
+    auto* A = (unsigned char*)b->arena;
+    for (auto& en : entries) en.state = (uint64_t)(uintptr_t)(A + P[(size_t)en.state].state_off);
+    {
+        size_t k = 0;
+        for (int mode = 0; mode < 3; mode++)
+            for (size_t i = 0; i < P.size(); i++) {
+                if (mode_of(P[i]) != mode) continue;
+                sentries[k].state = (uint64_t)(uintptr_t)(A + P[i].state_off);
+                sentries[k].probs = P[i].host_out ? (uint64_t)(uintptr_t)(A + P[i].probs_off)
+                                                  : (uint64_t)(uintptr_t)items[P[i].idx].probs_out;
+                k++;
+            }
+    }
+    for (auto& bp : P)
+        if (bp.host_out)
+            b->host_copies.push_back({items[bp.idx].probs_out, bp.probs_off, ((size_t)8) << bp.n});
+    // upload descriptors (synchronous copies from host vectors)
+    if (cudaMemcpy(A + ops_off, ops.data(), ops.size() * sizeof(DevOp), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(A + coef_off, coefs.data(), coefs.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(A + ent_off, entries.data(), entries.size() * sizeof(svk::BatchEntry), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(A + sent_off, sentries.data(), sentries.size() * sizeof(svk::StateEntry), cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+        return fail(SV_ERR_CUDA);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(SV_ERR_CUDA);
+    if (cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess)
+        return fail(SV_ERR_CUDA);
+    // capture: init (per mode) -> passes -> probabilities (per mode)
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(SV_ERR_CUDA);
+    cudaError_t ce = cudaSuccess;
+    const auto* d_ops = (const DevOp*)(A + ops_off);
+    const auto* d_ent = (const svk::BatchEntry*)(A + ent_off);
+    const auto* d_sent = (const svk::StateEntry*)(A + sent_off);
+    for (const auto& sl : slaunch)
+        if (ce == cudaSuccess) {
+            ce = svk::launch_init_multi(sl.dt, d_sent + sl.first, sl.count, sl.amps, b->stream, b->di);
+            b->n_launches++;
+        }
+    for (const auto& L : launches)
+        if (ce == cudaSuccess && L.n_ent > 0) {
+            ce = svk::launch_tile_pass(L.dt, L.arith, d_ent + L.ent_index, L.n_ent, L.tiles, L.max_m, L.kmax, d_ops,
+                                       A + coef_off, b->stream, b->di);
+            b->n_launches++;
+        }
+    for (const auto& sl : slaunch)
+        if (ce == cudaSuccess) {
+            ce = svk::launch_probs_multi(sl.dt, d_sent + sl.first, sl.count, sl.amps, b->stream, b->di);
+            b->n_launches++;
+        }
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(b->stream, &g);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(SV_ERR_CUDA);
+    }
+    b->graph = g;
+    if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) return fail(SV_ERR_CUDA);
+    (void)s;
+    *out = b;
+    return SV_OK;
+}
+
+int sv_batch_execute(sv_batch* b) {
+    if (!b || !b->exec) return SV_ERR_ARG;
+    if (cudaEventRecord(b->ev[0], b->stream) != cudaSuccess) return SV_ERR_CUDA;
+    if (cudaGraphLaunch(b->exec, b->stream) != cudaSuccess) return SV_ERR_CUDA;
+    if (cudaEventRecord(b->ev[1], b->stream) != cudaSuccess) return SV_ERR_CUDA;
+    for (const auto& hc : b->host_copies)
+        if (cudaMemcpyAsync(hc.dst, (unsigned char*)b->arena + hc.off, hc.bytes, cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess)
+            return SV_ERR_CUDA;
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SV_ERR_CUDA;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) b->last_ms = ms;
+    return SV_OK;
+}
+
+void sv_batch_destroy(sv_batch* b) {
+    if (b && b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+}
+
+int sv_batch_stats(const sv_batch* b, sv_batch_info* out) {
+    if (!b || !out) return SV_ERR_ARG;
+    out->n_items = b->n_items;
+    out->n_launches = b->n_launches;
+    out->arena_bytes = (double)b->arena_bytes;
+    out->last_ms = b->last_ms;
+    return SV_OK;
+}
+
+int sv_batch_run(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, int* item_status) {
+    sv_batch* b = nullptr;
+    int rc = sv_batch_create(items, n_items, opts, item_status, &b);
+    if (rc != SV_OK) return rc;
+    rc = sv_batch_execute(b);
+    sv_batch_destroy(b);
+    if (rc == SV_OK && item_status)
+        for (size_t i = 0; i < n_items; i++)
+            if (item_status[i] != SV_OK) rc = item_status[i];
+    return rc;
 }
 
 const char* sv_status_str(int st) {

@@ -30,4 +30,20 @@ struct DevPass {
     int8_t NL[kMaxQ];
 };
 
+// One (state, pass) pair of a tile-pass launch.  A launch sweeps the tiles of
+// all its entries as one flattened index space: entry e owns tiles
+// [tile_begin, tile_begin + p.tile_count).
+struct alignas(16) BatchEntry {
+    uint64_t state;       // device address of the state's amplitudes
+    uint64_t tile_begin;  // first flattened tile of this entry
+    DevPass p;
+};
+
+// One state of a multi-state init / probabilities launch.
+struct alignas(16) StateEntry {
+    uint64_t state;  // device address of the amplitudes
+    uint64_t probs;  // device address of its 2^n float64 probabilities
+    int32_t n, pad[3];
+};
+
 }  // namespace svk

@@ -33,7 +33,7 @@ __device__ __forceinline__ double fmaT(double a, double b, double c) { return fm
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ int swz(int j) {
-    constexpr int VS = (sizeof(R) == 4) ? 1 : 0;  // log2(amplitudes per 16-byte slot)
+    constexpr int VS = (sizeof(R) == 4) ? 1 : 0;  // log2(amplitudes per 16-byte slot); R = float or double
     int s = j >> VS;
     int h = (s >> 3) ^ (s >> 6) ^ (s >> 9) ^ (s >> 12);
     s ^= h & 7;
@@ -153,64 +153,6 @@ __device__ __forceinline__ void op_diag(Cx<R>* sm, int m, const DevOp& op, const
     }
 }
 
-template <typename R, int KMAX>
-__global__ void __launch_bounds__(kTileThreads) k_tile_pass(Cx<R>* __restrict__ st, const DevPass P,
-                                                            const DevOp* __restrict__ ops,
-                                                            const Cx<R>* __restrict__ coef) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Cx<R>* sm = reinterpret_cast<Cx<R>*>(smraw);
-    __shared__ uint64_t dep[2][32];  // deposit tables for the tile's high local bits
-    const int m = P.m, c = P.c, hb = m - c;
-    if (threadIdx.x < 64) {
-        const int w = threadIdx.x >> 5, v = threadIdx.x & 31;
-        uint64_t d = 0;
-        for (int b = 0; b < 5; b++) {
-            const int bit = w * 5 + b;
-            if (bit < hb && ((v >> b) & 1)) d |= 1ull << P.L[c + bit];
-        }
-        dep[w][v] = d;
-    }
-    __syncthreads();
-    constexpr int PER = 16 / sizeof(Cx<R>);      // amplitudes per 16-byte vector
-    const int nvec = (1 << m) / PER;
-    const int cmask = (1 << c) - 1;
-    for (uint64_t t = blockIdx.x; t < P.tile_count; t += gridDim.x) {
-        uint64_t base = 0;
-        for (int b = 0; b < P.n - m; b++)
-            if ((t >> b) & 1) base |= 1ull << P.NL[b];
-        // gather: runs of 2^c contiguous amplitudes
-        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-            const int j = v * PER;
-            const int r = j >> c;
-            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
-            const int4 val = *reinterpret_cast<const int4*>(st + gidx);
-            *reinterpret_cast<int4*>(sm + swz<R>(j)) = val;
-        }
-        __syncthreads();
-        for (int o = 0; o < P.n_ops; o++) {
-            const DevOp op = ops[P.op0 + o];
-            const Cx<R>* M = coef + op.coeff;
-            if (op.kind == OP_DIAG) {
-                op_diag<R>(sm, m, op, M, base);
-            } else {
-                if (op.k == 1) op_dense<1, R>(sm, m, op, M);
-                else if (op.k == 2) op_dense<(KMAX >= 2 ? 2 : 1), R>(sm, m, op, M);
-                else if (op.k == 3) op_dense<(KMAX >= 3 ? 3 : 1), R>(sm, m, op, M);
-                else if (op.k == 4) op_dense<(KMAX >= 4 ? 4 : 1), R>(sm, m, op, M);
-                else op_dense<(KMAX >= 5 ? 5 : 1), R>(sm, m, op, M);
-            }
-            __syncthreads();
-        }
-        for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
-            const int j = v * PER;
-            const int r = j >> c;
-            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
-            *reinterpret_cast<int4*>(st + gidx) = *reinterpret_cast<const int4*>(sm + swz<R>(j));
-        }
-        __syncthreads();
-    }
-}
-
 // ---------------------------------------------------------------------------
 // K5-df: tile pass for complex128 states with double-float arithmetic.
 //
@@ -234,6 +176,7 @@ __device__ __forceinline__ void d2df(double x, float& h, float& l) {
     const unsigned sign = hi32 & 0x80000000u;
     const int e = (int)((hi32 >> 20) & 0x7ff);
     if (e < 897) {  // |x| < 2^-126 (or zero): below float's normal range, dropped
+                    // (for 2^-126 <= |x| < 2^-103 only hi is kept: absolute error < 2^-126)
         h = 0.f;
         l = 0.f;
         return;
@@ -261,10 +204,12 @@ __device__ __forceinline__ double df2d(float h, float l) {
                                  ((unsigned long long)(eh + 896u) << 52) |
                                  ((unsigned long long)(hb & 0x7FFFFFu) << 29);
     const unsigned lb = __float_as_uint(l);
-    const unsigned el = (lb >> 23) & 0xffu;
-    if (el == 0u) return __longlong_as_double((long long)D);
-    // l in units of ulp_double(h) = 2^(eh - 179): k = ml * 2^(el - eh + 29), el <= eh - 24
-    const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | 0x800000u);
+    if ((lb & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)D);
+    // l = ml * 2^(el - 150) (subnormal l: no implicit bit, el taken as 1)
+    const unsigned el_raw = (lb >> 23) & 0xffu;
+    const unsigned el = el_raw ? el_raw : 1u;
+    const unsigned long long ml = (unsigned long long)((lb & 0x7FFFFFu) | (el_raw ? 0x800000u : 0u));
+    // in units of ulp_double(h) = 2^(eh - 179): k = ml * 2^(el - eh + 29), el <= eh - 24
     const int sh = (int)el - (int)eh + 29;
     unsigned long long k = sh >= 0 ? (ml << sh) : (sh > -40 ? (ml >> (-sh)) : 0ull);
     unsigned long long mag = D & 0x7FFFFFFFFFFFFFFFull;
@@ -381,59 +326,169 @@ __device__ __forceinline__ void op_diag_df(DF4* sm, int m, const DevOp& op, cons
     }
 }
 
-template <int KMAX>
-__global__ void __launch_bounds__(kTileThreads) k_tile_pass_df(Cx<double>* __restrict__ st, const DevPass P,
-                                                               const DevOp* __restrict__ ops,
-                                                               const DF4* __restrict__ coef) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    DF4* sm = reinterpret_cast<DF4*>(smraw);
-    __shared__ uint64_t dep[2][32];
-    const int m = P.m, c = P.c, hb = m - c;
-    if (threadIdx.x < 64) {
-        const int w = threadIdx.x >> 5, v = threadIdx.x & 31;
-        uint64_t d = 0;
-        for (int b = 0; b < 5; b++) {
-            const int bit = w * 5 + b;
-            if (bit < hb && ((v >> b) & 1)) d |= 1ull << P.L[c + bit];
+// ---------------------------------------------------------------------------
+// K5: the tile-pass kernel, shared by the three arithmetic modes.
+// ---------------------------------------------------------------------------
+enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2 };
+
+template <int MODE>
+struct TileTraits;
+template <>
+struct TileTraits<MODE_F32> {
+    using Store = Cx<float>;
+    using Smem = Cx<float>;
+    using Coef = Cx<float>;
+    using SwzT = float;
+};
+template <>
+struct TileTraits<MODE_F64> {
+    using Store = Cx<double>;
+    using Smem = Cx<double>;
+    using Coef = Cx<double>;
+    using SwzT = double;
+};
+template <>
+struct TileTraits<MODE_DF> {
+    using Store = Cx<double>;
+    using Smem = DF4;
+    using Coef = DF4;
+    using SwzT = double;
+};
+
+template <int MODE, int KMAX>
+__device__ __forceinline__ void apply_op(typename TileTraits<MODE>::Smem* sm, int m, const DevOp& op,
+                                         const typename TileTraits<MODE>::Coef* __restrict__ M, uint64_t base) {
+    if constexpr (MODE == MODE_DF) {
+        if (op.kind == OP_DIAG) {
+            op_diag_df(sm, m, op, M, base);
+        } else if (op.k == 1) {
+            op_dense_df<1>(sm, m, op, M);
+        } else if (op.k == 2) {
+            op_dense_df<(KMAX >= 2 ? 2 : 1)>(sm, m, op, M);
+        } else if (op.k == 3) {
+            op_dense_df<(KMAX >= 3 ? 3 : 1)>(sm, m, op, M);
+        } else if (op.k == 4) {
+            op_dense_df<(KMAX >= 4 ? 4 : 1)>(sm, m, op, M);
+        } else {
+            op_dense_df<(KMAX >= 5 ? 5 : 1)>(sm, m, op, M);
         }
-        dep[w][v] = d;
+    } else {
+        using R = typename TileTraits<MODE>::SwzT;
+        if (op.kind == OP_DIAG) {
+            op_diag<R>(sm, m, op, M, base);
+        } else if (op.k == 1) {
+            op_dense<1, R>(sm, m, op, M);
+        } else if (op.k == 2) {
+            op_dense<(KMAX >= 2 ? 2 : 1), R>(sm, m, op, M);
+        } else if (op.k == 3) {
+            op_dense<(KMAX >= 3 ? 3 : 1), R>(sm, m, op, M);
+        } else if (op.k == 4) {
+            op_dense<(KMAX >= 4 ? 4 : 1), R>(sm, m, op, M);
+        } else {
+            op_dense<(KMAX >= 5 ? 5 : 1), R>(sm, m, op, M);
+        }
     }
-    __syncthreads();
-    const int N = 1 << m;
-    const int cmask = (1 << c) - 1;
-    for (uint64_t t = blockIdx.x; t < P.tile_count; t += gridDim.x) {
-        uint64_t base = 0;
-        for (int b = 0; b < P.n - m; b++)
-            if ((t >> b) & 1) base |= 1ull << P.NL[b];
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            const int r = j >> c;
-            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
-            const Cx<double> a = st[gidx];
-            DF4 v;
-            d2df(a.re, v.rh, v.rl);
-            d2df(a.im, v.ih, v.il);
-            sm[swz<double>(j)] = v;
+}
+
+// Sweeps the tiles of every (state, pass) entry: gather the tile's 2^m
+// amplitudes (runs of 2^c contiguous ones, 16-byte loads) into shared memory,
+// apply the pass's ops in order, scatter the tile back.  Persistent: each CTA
+// strides over the flattened tile space of all entries.
+template <int MODE, int KMAX>
+__global__ void __launch_bounds__(kTileThreads)
+    k_tile_pass(const BatchEntry* __restrict__ E, int n_entries, uint64_t total_tiles, const DevOp* __restrict__ ops,
+                const typename TileTraits<MODE>::Coef* __restrict__ coef) {
+    using Tr = TileTraits<MODE>;
+    using Store = typename Tr::Store;
+    using Smem = typename Tr::Smem;
+    using SwzT = typename Tr::SwzT;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    Smem* sm = reinterpret_cast<Smem*>(smraw);
+    __shared__ uint64_t dep[2][32];  // deposit tables for the tile's high local bits
+    __shared__ __align__(16) DevPass P;
+    __shared__ uint64_t s_state, s_begin;
+    int cur = -1;
+    for (uint64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        int lo = 0, hi = n_entries - 1;  // entry owning tile t (uniform across the CTA)
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (E[mid].tile_begin <= t) lo = mid;
+            else hi = mid - 1;
         }
-        __syncthreads();
-        for (int o = 0; o < P.n_ops; o++) {
-            const DevOp op = ops[P.op0 + o];
-            const DF4* M = coef + op.coeff;
-            if (op.kind == OP_DIAG) {
-                op_diag_df(sm, m, op, M, base);
-            } else {
-                if (op.k == 1) op_dense_df<1>(sm, m, op, M);
-                else if (op.k == 2) op_dense_df<(KMAX >= 2 ? 2 : 1)>(sm, m, op, M);
-                else if (op.k == 3) op_dense_df<(KMAX >= 3 ? 3 : 1)>(sm, m, op, M);
-                else if (op.k == 4) op_dense_df<(KMAX >= 4 ? 4 : 1)>(sm, m, op, M);
-                else op_dense_df<(KMAX >= 5 ? 5 : 1)>(sm, m, op, M);
+        if (lo != cur) {
+            __syncthreads();
+            const unsigned* src = reinterpret_cast<const unsigned*>(&E[lo].p);
+            unsigned* dst = reinterpret_cast<unsigned*>(&P);
+            for (int i = threadIdx.x; i < (int)(sizeof(DevPass) / 4); i += blockDim.x) dst[i] = src[i];
+            if (threadIdx.x == 0) {
+                s_state = E[lo].state;
+                s_begin = E[lo].tile_begin;
             }
             __syncthreads();
+            if (threadIdx.x < 64) {
+                const int w = threadIdx.x >> 5, v = threadIdx.x & 31, hb = P.m - P.c;
+                uint64_t d = 0;
+                for (int b = 0; b < 5; b++) {
+                    const int bit = w * 5 + b;
+                    if (bit < hb && ((v >> b) & 1)) d |= 1ull << P.L[P.c + bit];
+                }
+                dep[w][v] = d;
+            }
+            __syncthreads();
+            cur = lo;
         }
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            const int r = j >> c;
-            const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
-            const DF4 v = sm[swz<double>(j)];
-            st[gidx] = Cx<double>{df2d(v.rh, v.rl), df2d(v.ih, v.il)};
+        Store* st = reinterpret_cast<Store*>(s_state);
+        const int m = P.m, c = P.c;
+        const int cmask = (1 << c) - 1;
+        const uint64_t tl = t - s_begin;
+        uint64_t base = 0;
+        for (int b = 0; b < P.n - m; b++)
+            if ((tl >> b) & 1) base |= 1ull << P.NL[b];
+        if constexpr (MODE == MODE_DF) {
+            const int N = 1 << m;
+            for (int j = threadIdx.x; j < N; j += blockDim.x) {
+                const int r = j >> c;
+                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                const Cx<double> a = st[gidx];
+                DF4 v;
+                d2df(a.re, v.rh, v.rl);
+                d2df(a.im, v.ih, v.il);
+                sm[swz<double>(j)] = v;
+            }
+        } else {
+            constexpr int PER = 16 / sizeof(Store);  // amplitudes per 16-byte vector
+            const int nvec = (1 << m) / PER;
+            for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+                const int j = v * PER;
+                const int r = j >> c;
+                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                *reinterpret_cast<int4*>(sm + swz<SwzT>(j)) = *reinterpret_cast<const int4*>(st + gidx);
+            }
+        }
+        __syncthreads();
+        const int n_ops = P.n_ops, op0 = P.op0;
+        for (int o = 0; o < n_ops; o++) {
+            const DevOp op = ops[op0 + o];
+            apply_op<MODE, KMAX>(sm, m, op, coef + op.coeff, base);
+            __syncthreads();
+        }
+        if constexpr (MODE == MODE_DF) {
+            const int N = 1 << m;
+            for (int j = threadIdx.x; j < N; j += blockDim.x) {
+                const int r = j >> c;
+                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                const DF4 v = sm[swz<double>(j)];
+                st[gidx] = Cx<double>{df2d(v.rh, v.rl), df2d(v.ih, v.il)};
+            }
+        } else {
+            constexpr int PER = 16 / sizeof(Store);
+            const int nvec = (1 << m) / PER;
+            for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
+                const int j = v * PER;
+                const int r = j >> c;
+                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                *reinterpret_cast<int4*>(st + gidx) = *reinterpret_cast<const int4*>(sm + swz<SwzT>(j));
+            }
         }
         __syncthreads();
     }
@@ -577,6 +632,34 @@ __global__ void k_zero_u64(unsigned long long* p, uint64_t n) {
 }
 
 // ---------------------------------------------------------------------------
+// Multi-state init and probabilities (batched form): each CTA walks the
+// entries in order and grid-strides over each entry's elements.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_init_multi(const StateEntry* __restrict__ E, int n_entries) {
+    constexpr int PER = 16 / sizeof(Cx<R>);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (int e = 0; e < n_entries; e++) {
+        Cx<R>* a = reinterpret_cast<Cx<R>*>(E[e].state);
+        const uint64_t nvec = (1ull << E[e].n) / PER;
+        for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += stride)
+            reinterpret_cast<int4*>(a)[v] = (v == 0) ? unit_vector16<R>(0) : make_int4(0, 0, 0, 0);
+    }
+}
+
+template <typename R>
+__global__ void k_probs_multi(const StateEntry* __restrict__ E, int n_entries) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (int e = 0; e < n_entries; e++) {
+        const Cx<R>* a = reinterpret_cast<const Cx<R>*>(E[e].state);
+        double* p = reinterpret_cast<double*>(E[e].probs);
+        const uint64_t dim = 1ull << E[e].n;
+        for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride)
+            p[i] = prob_of<R>(a[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
 static unsigned grid_for(uint64_t work, int threads, const DevInfo& di, int per_sm = 8) {
@@ -596,73 +679,69 @@ cudaError_t launch_init(int dt, void* amp, int n, uint64_t basis, cudaStream_t s
     return cudaGetLastError();
 }
 
-template <typename R, int KMAX>
-static cudaError_t tile_pass_impl(void* amp, const DevPass& p, const DevOp* d_ops, const void* d_coef,
-                                  cudaStream_t s, const DevInfo& di) {
-    const size_t smem = ((size_t)1 << p.m) * sizeof(Cx<R>);
+template <int MODE, int KMAX>
+static cudaError_t tile_pass_impl(const BatchEntry* d_entries, int n_entries, uint64_t total_tiles, int max_m,
+                                  const DevOp* d_ops, const void* d_coef, cudaStream_t s, const DevInfo& di) {
+    using Tr = TileTraits<MODE>;
+    const size_t smem = ((size_t)1 << max_m) * sizeof(typename Tr::Smem);
     static int configured_dev = -1;
     if (configured_dev != di.device) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_pass<R, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tile_pass<MODE, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(di.smem_optin - 2048));
         if (e != cudaSuccess) return e;
         configured_dev = di.device;
     }
     int per_sm = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<R, KMAX>, kTileThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<MODE, KMAX>, kTileThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = (uint64_t)di.sms * per_sm;
-    if (grid > p.tile_count) grid = p.tile_count;
-    k_tile_pass<R, KMAX><<<(unsigned)grid, kTileThreads, smem, s>>>((Cx<R>*)amp, p, d_ops, (const Cx<R>*)d_coef);
+    if (grid > total_tiles) grid = total_tiles;
+    k_tile_pass<MODE, KMAX><<<(unsigned)grid, kTileThreads, smem, s>>>(
+        d_entries, n_entries, total_tiles, d_ops, (const typename Tr::Coef*)d_coef);
     return cudaGetLastError();
 }
 
-template <typename R>
-static cudaError_t tile_pass_k(int kmax, void* amp, const DevPass& p, const DevOp* d_ops, const void* d_coef,
-                               cudaStream_t s, const DevInfo& di) {
+template <int MODE>
+static cudaError_t tile_pass_mode(int kmax, const BatchEntry* d_entries, int n_entries, uint64_t total_tiles,
+                                  int max_m, const DevOp* d_ops, const void* d_coef, cudaStream_t s,
+                                  const DevInfo& di) {
     switch (kmax) {
-        case 1: return tile_pass_impl<R, 1>(amp, p, d_ops, d_coef, s, di);
-        case 2: return tile_pass_impl<R, 2>(amp, p, d_ops, d_coef, s, di);
-        case 3: return tile_pass_impl<R, 3>(amp, p, d_ops, d_coef, s, di);
-        case 4: return tile_pass_impl<R, 4>(amp, p, d_ops, d_coef, s, di);
-        default: return tile_pass_impl<R, 5>(amp, p, d_ops, d_coef, s, di);
+        case 1: return tile_pass_impl<MODE, 1>(d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+        case 2: return tile_pass_impl<MODE, 2>(d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+        case 3: return tile_pass_impl<MODE, 3>(d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+        case 4: return tile_pass_impl<MODE, 4>(d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+        default: return tile_pass_impl<MODE, 5>(d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
     }
 }
 
-template <int KMAX>
-static cudaError_t tile_pass_df_impl(void* amp, const DevPass& p, const DevOp* d_ops, const void* d_coef,
-                                     cudaStream_t s, const DevInfo& di) {
-    const size_t smem = ((size_t)1 << p.m) * sizeof(DF4);
-    static int configured_dev = -1;
-    if (configured_dev != di.device) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_pass_df<KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(di.smem_optin - 2048));
-        if (e != cudaSuccess) return e;
-        configured_dev = di.device;
-    }
-    int per_sm = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass_df<KMAX>, kTileThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    uint64_t grid = (uint64_t)di.sms * per_sm;
-    if (grid > p.tile_count) grid = p.tile_count;
-    k_tile_pass_df<KMAX><<<(unsigned)grid, kTileThreads, smem, s>>>((Cx<double>*)amp, p, d_ops, (const DF4*)d_coef);
+cudaError_t launch_tile_pass(int dt, int arith, const BatchEntry* d_entries, int n_entries, uint64_t total_tiles,
+                             int max_m, int kmax, const DevOp* d_ops, const void* d_coef, cudaStream_t s,
+                             const DevInfo& di) {
+    if (n_entries <= 0 || total_tiles == 0) return cudaSuccess;
+    if (dt == SV_C64)
+        return tile_pass_mode<MODE_F32>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+    if (arith == SV_ARITH_DF64)
+        return tile_pass_mode<MODE_DF>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+    return tile_pass_mode<MODE_F64>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+}
+
+cudaError_t launch_init_multi(int dt, const StateEntry* d_entries, int n_entries, uint64_t total_amps,
+                              cudaStream_t s, const DevInfo& di) {
+    if (n_entries <= 0) return cudaSuccess;
+    const unsigned grid = grid_for(total_amps / 2 + 1, 256, di, 8);
+    if (dt == SV_C64) k_init_multi<float><<<grid, 256, 0, s>>>(d_entries, n_entries);
+    else k_init_multi<double><<<grid, 256, 0, s>>>(d_entries, n_entries);
     return cudaGetLastError();
 }
 
-cudaError_t launch_tile_pass(int dt, int arith, void* amp, const DevPass& p, const DevOp* d_ops,
-                             const void* d_coef, cudaStream_t s, const DevInfo& di) {
-    if (dt == SV_C128 && arith == SV_ARITH_DF64) {
-        switch (p.kmax) {
-            case 1: return tile_pass_df_impl<1>(amp, p, d_ops, d_coef, s, di);
-            case 2: return tile_pass_df_impl<2>(amp, p, d_ops, d_coef, s, di);
-            case 3: return tile_pass_df_impl<3>(amp, p, d_ops, d_coef, s, di);
-            case 4: return tile_pass_df_impl<4>(amp, p, d_ops, d_coef, s, di);
-            default: return tile_pass_df_impl<5>(amp, p, d_ops, d_coef, s, di);
-        }
-    }
-    if (dt == SV_C64) return tile_pass_k<float>(p.kmax, amp, p, d_ops, d_coef, s, di);
-    return tile_pass_k<double>(p.kmax, amp, p, d_ops, d_coef, s, di);
+cudaError_t launch_probs_multi(int dt, const StateEntry* d_entries, int n_entries, uint64_t total_amps,
+                               cudaStream_t s, const DevInfo& di) {
+    if (n_entries <= 0) return cudaSuccess;
+    const unsigned grid = grid_for(total_amps, 256, di, 8);
+    if (dt == SV_C64) k_probs_multi<float><<<grid, 256, 0, s>>>(d_entries, n_entries);
+    else k_probs_multi<double><<<grid, 256, 0, s>>>(d_entries, n_entries);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_probs(int dt, const void* amp, uint64_t i0, uint64_t len, double* p, cudaStream_t s,

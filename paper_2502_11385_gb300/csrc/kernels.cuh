@@ -21,11 +21,21 @@ constexpr int kTileThreads = 256;
 // amp := e_basis (K1).
 cudaError_t launch_init(int dt, void* amp, int n, uint64_t basis, cudaStream_t s, const DevInfo& di);
 
-// One tile pass (K5): every tile of the state is gathered into shared memory,
-// the pass's ops are applied in order, and the tile is written back.
-// arith: SV_ARITH_NATIVE or SV_ARITH_DF64 (complex128 only).
-cudaError_t launch_tile_pass(int dt, int arith, void* amp, const DevPass& p, const DevOp* d_ops,
-                             const void* d_coef, cudaStream_t s, const DevInfo& di);
+// One tile-pass launch (K5) over n_entries (state, pass) pairs in device
+// memory: every tile of every entry is gathered into shared memory, the
+// entry's ops are applied in order, and the tile is written back.
+// total_tiles = sum of the entries' tile counts; max_m / kmax = largest tile
+// and dense block among the entries; arith: SV_ARITH_NATIVE or SV_ARITH_DF64
+// (complex128 only).
+cudaError_t launch_tile_pass(int dt, int arith, const BatchEntry* d_entries, int n_entries, uint64_t total_tiles,
+                             int max_m, int kmax, const DevOp* d_ops, const void* d_coef, cudaStream_t s,
+                             const DevInfo& di);
+
+// Batched form: every entry's state := |0...0> / every entry's probabilities.
+cudaError_t launch_init_multi(int dt, const StateEntry* d_entries, int n_entries, uint64_t total_amps,
+                              cudaStream_t s, const DevInfo& di);
+cudaError_t launch_probs_multi(int dt, const StateEntry* d_entries, int n_entries, uint64_t total_amps,
+                               cudaStream_t s, const DevInfo& di);
 
 // p[i - i0] = |amp_i|^2 for i in [i0, i0 + len) (K7, probability part).
 cudaError_t launch_probs(int dt, const void* amp, uint64_t i0, uint64_t len, double* p,

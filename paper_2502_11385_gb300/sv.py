@@ -50,6 +50,11 @@ class BatchItem(ctypes.Structure):
                 ("n_gates", ctypes.c_size_t), ("probs_out", ctypes.c_void_p), ("probs_on_device", ctypes.c_int32)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int32), ("n_launches", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_double), ("last_ms", ctypes.c_double)]
+
+
 class PlanSummary(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
                 ("tile_qubits", ctypes.c_int32), ("flops", ctypes.c_double), ("model_ms", ctypes.c_double)]
@@ -73,6 +78,11 @@ _SIGS = {
     "sv_norm": ([_vp, ctypes.POINTER(ctypes.c_double)], _i32),
     "sv_last_stats": ([_vp, ctypes.POINTER(ApplyStats)], _i32),
     "sv_batch_run": ([ctypes.POINTER(BatchItem), _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(ctypes.c_int)], _i32),
+    "sv_batch_create": ([ctypes.POINTER(BatchItem), _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(ctypes.c_int),
+                         ctypes.POINTER(_vp)], _i32),
+    "sv_batch_execute": ([_vp], _i32),
+    "sv_batch_destroy": ([_vp], None),
+    "sv_batch_stats": ([_vp, ctypes.POINTER(BatchInfo)], _i32),
     "sv_status_str": ([_i32], ctypes.c_char_p),
     "sv_version": ([], ctypes.c_char_p),
     "sv_plan_build": ([_i32, _i32, _vp, _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(_vp)], _i32),
@@ -261,8 +271,7 @@ def simulate(n: int, gates, dtype="c128", opts=None):
         return s.amplitudes(), s.probabilities()
 
 
-def batch_run(items, opts=None):
-    """items: list of (n, dtype, gates, probs_out or None).  Returns (outputs, statuses)."""
+def _batch_items(items):
     arr = (BatchItem * len(items))()
     keep, outs = [], []
     for i, (n, dtype, gates, out) in enumerate(items):
@@ -275,9 +284,56 @@ def batch_run(items, opts=None):
         keep.append(g)
         outs.append(out)
         arr[i] = BatchItem(n, DTYPES[dtype], g.ctypes.data if len(g) else None, len(g), p, dev)
-    st = (ctypes.c_int * len(items))()
+    return arr, keep, outs
+
+
+def batch_run(items, opts=None):
+    """Batched form in one call.  items: list of (n, dtype, gates, probs_out
+    or None).  Returns (outputs, per-item statuses)."""
+    arr, _keep, outs = _batch_items(items)
+    st = (ctypes.c_int * max(1, len(items)))()
     _lib.sv_batch_run(arr, len(items), _opts_ptr(opts), st)
-    return outs, list(st)
+    return outs, list(st)[: len(items)]
+
+
+class Batch:
+    """A prepared batch (sv_batch_create): its CUDA graph is replayed by
+    execute(); outputs are refreshed in place on every execute()."""
+
+    def __init__(self, items, opts=None):
+        self._arr, self._keep, self.outputs = _batch_items(items)
+        st = (ctypes.c_int * max(1, len(items)))()
+        h = _vp()
+        rc = _lib.sv_batch_create(self._arr, len(items), _opts_ptr(opts), st, ctypes.byref(h))
+        self.status = list(st)[: len(items)]
+        _check(rc, "sv_batch_create")
+        self._h = h
+
+    def execute(self):
+        _check(_lib.sv_batch_execute(self._h), "sv_batch_execute")
+        return self.outputs
+
+    def stats(self) -> dict:
+        b = BatchInfo()
+        _check(_lib.sv_batch_stats(self._h, ctypes.byref(b)), "sv_batch_stats")
+        return {f: getattr(b, f) for f, _ in BatchInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.sv_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Plan:

@@ -283,3 +283,55 @@ def test_df64_conversion_roundtrip(sv):
         rel = np.abs(got[big] - want[big]) / np.abs(want[big])
         assert rel.max() <= 2.0 ** -46, rel.max()
         assert np.all(got[np.abs(want) < 2.0 ** -126] == 0)
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+def test_batch_matches_solo_bitwise_and_oracle(sv):
+    rng = np.random.default_rng(9)
+    items, solo = [], []
+    specs = [(9, "c64"), (12, "c128"), (14, "c64"), (10, "c128"), (16, "c128"), (5, "c64"), (13, "c128")]
+    for i, (n, dt) in enumerate(specs):
+        g = _random_circuit(n, 60 + 5 * i, 400 + i)
+        items.append((n, dt, g, None))
+    for arith in (sv.ARITH_NATIVE, sv.ARITH_DF64):
+        opts = sv.run_opts(arith=arith)
+        with sv.Batch(items, opts) as b:
+            assert b.status == [0] * len(items)
+            outs = b.execute()
+            outs2 = [o.copy() for o in b.execute()]  # replay of the captured graph
+            st = b.stats()
+            assert st["n_items"] == len(items) and st["n_launches"] >= 3
+        for (n, dt, g, _), o, o2 in zip(items, outs, outs2):
+            with sv.State(n, dt) as s:
+                s.apply_circuit(g, opts)
+                p = s.probabilities()
+            assert np.array_equal(o, p)            # same plan, same kernels: bitwise
+            assert np.array_equal(o, o2)
+            pref = oracle.probabilities(oracle.run(n, g))
+            assert np.abs(o - pref).max() <= 4 * TOL[dt]
+
+
+def test_batch_device_outputs_and_invalid_items(sv):
+    import torch
+    g_ok = W.brickwork(11, 4, 3)
+    dev = torch.empty(1 << 11, dtype=torch.float64, device="cuda")
+    items = [(11, "c128", g_ok, dev), (11, "c64", W.gates([(W.H, 11, -1)]), None), (8, "c64", W.ghz_prefix(8), None)]
+    outs, status = sv.batch_run(items)
+    assert status[0] == 0 and status[1] == sv.SV_ERR_QUBIT and status[2] == 0
+    ref = oracle.probabilities(oracle.run(11, g_ok))
+    assert np.abs(dev.cpu().numpy() - ref).max() <= 4e-12
+    assert abs(outs[2][0] - 0.5) < 1e-6 and abs(outs[2][-1] - 0.5) < 1e-6
+
+
+def test_cut_variants_batched(sv):
+    """Cut-subcircuit variants of a small cuttable brickwork (12 qubits, 2 cut
+    wires): all 9 upstream and 16 downstream variants in one batch."""
+    cc = W.cuttable_brickwork(12, 6, 11, cut_lo=5, n_cuts=2, switch_layer=3)
+    ups, downs = cc.upstream_variants(), cc.downstream_variants()
+    items = [(cc.width_a, "c128", g, None) for g in ups] + [(cc.width_b, "c64", g, None) for g in downs]
+    outs, status = sv.batch_run(items, sv.run_opts(arith=sv.ARITH_DF64))
+    assert all(s == 0 for s in status)
+    for (n, dt, g, _), o in zip(items, outs):
+        assert np.abs(o - oracle.probabilities(oracle.run(n, g))).max() <= 4 * TOL[dt]
