@@ -115,6 +115,10 @@ int sv_create_on(void* dev_ptr, size_t bytes, int n_qubits, int dt,
 /* Frees the handle and, unless created by sv_create_on, its buffer. */
 void sv_destroy(sv_state* s);
 
+/* Points a handle made by sv_create_on at another caller-owned buffer (same
+ * rules as sv_create_on; the stream is kept), reusing its workspaces. */
+int sv_rebind(sv_state* s, void* dev_ptr, size_t bytes, int n_qubits, int dt);
+
 int sv_num_qubits(const sv_state* s);
 int sv_dtype_of(const sv_state* s);
 /* Device pointer of the amplitudes (for zero-copy interop). */
@@ -203,6 +207,18 @@ int sv_batch_create(const sv_batch_item* items, size_t n_items,
                     const sv_run_opts* opts, int* item_status, sv_batch** out);
 int sv_batch_execute(sv_batch* b);
 void sv_batch_destroy(sv_batch* b);
+
+/* Arena variant for callers that manage device memory themselves (a serving
+ * loop on a caching allocator: freeing device memory with cudaFree stalls the
+ * whole device).  sv_batch_arena_bytes reports the bytes a batch of these
+ * items needs; sv_batch_create_in builds the batch inside the caller's
+ * device buffer (256-byte aligned, at least that many bytes), which the
+ * caller keeps alive until sv_batch_destroy and frees afterwards. */
+int sv_batch_arena_bytes(const sv_batch_item* items, size_t n_items,
+                         const sv_run_opts* opts, size_t* bytes);
+int sv_batch_create_in(const sv_batch_item* items, size_t n_items,
+                       const sv_run_opts* opts, int* item_status,
+                       void* arena, size_t arena_bytes, sv_batch** out);
 
 /* Counts of a batch: launches in its graph, device bytes it holds, and the
  * duration of the last sv_batch_execute measured with CUDA events. */

@@ -353,6 +353,20 @@ int sv_create_on(void* dev_ptr, size_t bytes, int n, int dt, void* stream, sv_st
     return SV_OK;
 }
 
+int sv_rebind(sv_state* s, void* dev_ptr, size_t bytes, int n, int dt) {
+    if (!s || s->owned || !dev_ptr || ((uintptr_t)dev_ptr & 15)) return SV_ERR_ARG;
+    if (n < 1 || n > svp::kMaxQubits || !dt_ok(dt)) return SV_ERR_ARG;
+    if (bytes != sv_state_bytes(n, dt)) return SV_ERR_SIZE;
+    if (s->stream) SV_TRY(cudaStreamSynchronize(s->stream));
+    s->amp = dev_ptr;
+    s->n = n;
+    s->dt = dt;
+    s->bytes = bytes;
+    s->failed = false;
+    s->last = sv_apply_stats{};
+    return SV_OK;
+}
+
 void sv_destroy(sv_state* s) {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
@@ -485,6 +499,7 @@ struct sv_batch {
     cudaStream_t stream = nullptr;
     void* arena = nullptr;      // states, device-side probabilities, descriptors
     size_t arena_bytes = 0;
+    bool own_arena = true;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -511,7 +526,7 @@ void batch_free(sv_batch* b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    if (b->arena) cudaFree(b->arena);
+    if (b->arena && b->own_arena) cudaFree(b->arena);
     for (auto& e : b->ev)
         if (e) cudaEventDestroy(e);
     if (b->stream) cudaStreamDestroy(b->stream);
@@ -522,9 +537,11 @@ void batch_free(sv_batch* b) {
 
 extern "C" {
 
-int sv_batch_create(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, int* item_status,
-                    sv_batch** out) {
-    if (!out || (n_items && !items)) return SV_ERR_ARG;
+// Builds a batch; with ext_arena == nullptr it allocates its own arena, with
+// size_only it only reports the arena size in *size_out.
+static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, int* item_status,
+                       void* ext_arena, size_t ext_bytes, bool size_only, size_t* size_out, sv_batch** out) {
+    if ((!out && !size_only) || (n_items && !items)) return SV_ERR_ARG;
     sv_batch* b = new (std::nothrow) sv_batch();
     if (!b) return SV_ERR_OOM;
     sv_state* s = nullptr;  // for SV_TRY
@@ -648,12 +665,22 @@ int sv_batch_create(const sv_batch_item* items, size_t n_items, const sv_run_opt
     const size_t sent_off = off;
     off += align256(sentries.size() * sizeof(svk::StateEntry) + 16);
     b->arena_bytes = off;
-    size_t fr = 0, to = 0;
-    if (cudaMemGetInfo(&fr, &to) == cudaSuccess && off > fr) return fail(SV_ERR_OOM);
-    cudaError_t e = cudaMalloc(&b->arena, off);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA);
+    if (size_only) {
+        *size_out = off;
+        return fail(SV_OK);
+    }
+    if (ext_arena) {
+        if (ext_bytes < off || ((uintptr_t)ext_arena & 255)) return fail(SV_ERR_SIZE);
+        b->arena = ext_arena;
+        b->own_arena = false;
+    } else {
+        size_t fr = 0, to = 0;
+        if (cudaMemGetInfo(&fr, &to) == cudaSuccess && off > fr) return fail(SV_ERR_OOM);
+        cudaError_t e = cudaMalloc(&b->arena, off);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? SV_ERR_OOM : SV_ERR_CUDA);
+        }
     }
     auto* A = (unsigned char*)b->arena;
     for (auto& en : entries) en.state = (uint64_t)(uintptr_t)(A + P[(size_t)en.state].state_off);
@@ -716,6 +743,22 @@ int sv_batch_create(const sv_batch_item* items, size_t n_items, const sv_run_opt
     (void)s;
     *out = b;
     return SV_OK;
+}
+
+int sv_batch_create(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, int* item_status,
+                    sv_batch** out) {
+    return batch_build(items, n_items, opts, item_status, nullptr, 0, false, nullptr, out);
+}
+
+int sv_batch_arena_bytes(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, size_t* bytes) {
+    if (!bytes) return SV_ERR_ARG;
+    return batch_build(items, n_items, opts, nullptr, nullptr, 0, true, bytes, nullptr);
+}
+
+int sv_batch_create_in(const sv_batch_item* items, size_t n_items, const sv_run_opts* opts, int* item_status,
+                       void* arena, size_t arena_bytes, sv_batch** out) {
+    if (!arena) return SV_ERR_ARG;
+    return batch_build(items, n_items, opts, item_status, arena, arena_bytes, false, nullptr, out);
 }
 
 int sv_batch_execute(sv_batch* b) {

@@ -81,9 +81,28 @@ __device__ __forceinline__ int group_offset(int b, const int (&pm)[K]) {
     return off;
 }
 
+// Groups a thread handles per step of a k-qubit dense op: each coefficient
+// load then feeds G independent groups.
+// (Native float64 is bound by the FP64 pipe, so it keeps one group per step.)
+template <int K, typename R>
+struct GroupsPerStep {
+    static constexpr int value = sizeof(R) == 8 ? 1 : (K <= 2 ? 4 : (K == 3 ? 2 : 1));
+};
+
+template <int K>
+__device__ __forceinline__ int insert_zero_bits(int g, const int (&pos)[K]) {
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        const int p = pos[j];
+        g = ((g >> p) << (p + 1)) | (g & ((1 << p) - 1));
+    }
+    return g;
+}
+
 template <int K, typename R>
 __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, const Cx<R>* __restrict__ M) {
     constexpr int D = 1 << K;
+    constexpr int G = GroupsPerStep<K, R>::value;
     int pos[K], pm[K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
@@ -91,28 +110,38 @@ __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, cons
         pm[j] = 1 << pos[j];
     }
     const int ng = 1 << (m - K);
-    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-        int base = g;
+    for (int g0 = threadIdx.x; g0 < ng; g0 += blockDim.x * G) {
+        int base[G];
+        bool ok[G];
+        Cx<R> a[G][D];
 #pragma unroll
-        for (int j = 0; j < K; j++) {
-            const int p = pos[j];
-            base = ((base >> p) << (p + 1)) | (base & ((1 << p) - 1));
+        for (int q = 0; q < G; q++) {
+            const int g = g0 + q * blockDim.x;
+            ok[q] = g < ng;
+            base[q] = insert_zero_bits<K>(ok[q] ? g : 0, pos);
+#pragma unroll
+            for (int b = 0; b < D; b++) a[q][b] = sm[swz<R>(base[q] | group_offset<K>(b, pm))];
         }
-        Cx<R> a[D];
-#pragma unroll
-        for (int b = 0; b < D; b++) a[b] = sm[swz<R>(base | group_offset<K>(b, pm))];
 #pragma unroll(K <= 2 ? D : 1)
         for (int r = 0; r < D; r++) {
-            R re = R(0), im = R(0);
+            R re[G], im[G];
+#pragma unroll
+            for (int q = 0; q < G; q++) re[q] = im[q] = R(0);
 #pragma unroll
             for (int c = 0; c < D; c++) {
                 const Cx<R> u = M[r * D + c];
-                re = fmaT(u.re, a[c].re, re);
-                re = fmaT(-u.im, a[c].im, re);
-                im = fmaT(u.re, a[c].im, im);
-                im = fmaT(u.im, a[c].re, im);
+#pragma unroll
+                for (int q = 0; q < G; q++) {
+                    re[q] = fmaT(u.re, a[q][c].re, re[q]);
+                    re[q] = fmaT(-u.im, a[q][c].im, re[q]);
+                    im[q] = fmaT(u.re, a[q][c].im, im[q]);
+                    im[q] = fmaT(u.im, a[q][c].re, im[q]);
+                }
             }
-            sm[swz<R>(base | group_offset<K>(r, pm))] = Cx<R>{re, im};
+            const int off = group_offset<K>(r, pm);
+#pragma unroll
+            for (int q = 0; q < G; q++)
+                if (ok[q]) sm[swz<R>(base[q] | off)] = Cx<R>{re[q], im[q]};
         }
     }
 }
@@ -242,26 +271,16 @@ __device__ __forceinline__ void df_norm(float& h, float& l) {
     h = s;
 }
 
-// out = sum_c M[c] * a[c] over complex double-floats
-template <int D>
-__device__ __forceinline__ DF4 df_dot(const DF4* __restrict__ Mrow, const DF4 (&a)[D]) {
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-#pragma unroll
-    for (int c = 0; c < D; c++) {
-        const DF4 u = Mrow[c];
-        df_mac(rh, rl, u.rh, u.rl, a[c].rh, a[c].rl);
-        df_mac(rh, rl, -u.ih, -u.il, a[c].ih, a[c].il);
-        df_mac(ih, il, u.rh, u.rl, a[c].ih, a[c].il);
-        df_mac(ih, il, u.ih, u.il, a[c].rh, a[c].rl);
-    }
-    df_norm(rh, rl);
-    df_norm(ih, il);
-    return DF4{rh, rl, ih, il};
+// (sh, sl) = x * y as an unnormalised double-float (TwoProd + cross terms).
+__device__ __forceinline__ void df_mul(float& sh, float& sl, float xh, float xl, float yh, float yl) {
+    sh = __fmul_rn(xh, yh);
+    sl = fmaf(xh, yl, fmaf(xl, yh, fmaf(xh, yh, -sh)));
 }
 
 template <int K>
 __device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, const DF4* __restrict__ M) {
     constexpr int D = 1 << K;
+    constexpr int G = K <= 2 ? 2 : 1;
     int pos[K], pm[K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
@@ -269,18 +288,51 @@ __device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, con
         pm[j] = 1 << pos[j];
     }
     const int ng = 1 << (m - K);
-    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-        int base = g;
+    for (int g0 = threadIdx.x; g0 < ng; g0 += blockDim.x * G) {
+        int base[G];
+        bool ok[G];
+        DF4 a[G][D];
 #pragma unroll
-        for (int j = 0; j < K; j++) {
-            const int p = pos[j];
-            base = ((base >> p) << (p + 1)) | (base & ((1 << p) - 1));
+        for (int q = 0; q < G; q++) {
+            const int g = g0 + q * blockDim.x;
+            ok[q] = g < ng;
+            base[q] = insert_zero_bits<K>(ok[q] ? g : 0, pos);
+#pragma unroll
+            for (int b = 0; b < D; b++) a[q][b] = sm[swz<double>(base[q] | group_offset<K>(b, pm))];
         }
-        DF4 a[D];
-#pragma unroll
-        for (int b = 0; b < D; b++) a[b] = sm[swz<double>(base | group_offset<K>(b, pm))];
 #pragma unroll(K <= 1 ? D : 1)
-        for (int r = 0; r < D; r++) sm[swz<double>(base | group_offset<K>(r, pm))] = df_dot<D>(M + r * D, a);
+        for (int r = 0; r < D; r++) {
+            const DF4* Mrow = M + r * D;
+            float rh[G], rl[G], ih[G], il[G];
+            {
+                const DF4 u = Mrow[0];
+#pragma unroll
+                for (int q = 0; q < G; q++) {
+                    df_mul(rh[q], rl[q], u.rh, u.rl, a[q][0].rh, a[q][0].rl);
+                    df_mac(rh[q], rl[q], -u.ih, -u.il, a[q][0].ih, a[q][0].il);
+                    df_mul(ih[q], il[q], u.rh, u.rl, a[q][0].ih, a[q][0].il);
+                    df_mac(ih[q], il[q], u.ih, u.il, a[q][0].rh, a[q][0].rl);
+                }
+            }
+#pragma unroll
+            for (int c = 1; c < D; c++) {
+                const DF4 u = Mrow[c];
+#pragma unroll
+                for (int q = 0; q < G; q++) {
+                    df_mac(rh[q], rl[q], u.rh, u.rl, a[q][c].rh, a[q][c].rl);
+                    df_mac(rh[q], rl[q], -u.ih, -u.il, a[q][c].ih, a[q][c].il);
+                    df_mac(ih[q], il[q], u.rh, u.rl, a[q][c].ih, a[q][c].il);
+                    df_mac(ih[q], il[q], u.ih, u.il, a[q][c].rh, a[q][c].rl);
+                }
+            }
+            const int off = group_offset<K>(r, pm);
+#pragma unroll
+            for (int q = 0; q < G; q++) {
+                df_norm(rh[q], rl[q]);
+                df_norm(ih[q], il[q]);
+                if (ok[q]) sm[swz<double>(base[q] | off)] = DF4{rh[q], rl[q], ih[q], il[q]};
+            }
+        }
     }
 }
 

@@ -81,6 +81,10 @@ _SIGS = {
     "sv_batch_create": ([ctypes.POINTER(BatchItem), _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(ctypes.c_int),
                          ctypes.POINTER(_vp)], _i32),
     "sv_batch_execute": ([_vp], _i32),
+    "sv_batch_arena_bytes": ([ctypes.POINTER(BatchItem), _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(_sz)], _i32),
+    "sv_batch_create_in": ([ctypes.POINTER(BatchItem), _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(ctypes.c_int),
+                            _vp, _sz, ctypes.POINTER(_vp)], _i32),
+    "sv_rebind": ([_vp, _vp, _sz, _i32, _i32], _i32),
     "sv_batch_destroy": ([_vp], None),
     "sv_batch_stats": ([_vp, ctypes.POINTER(BatchInfo)], _i32),
     "sv_status_str": ([_i32], ctypes.c_char_p),
@@ -185,6 +189,14 @@ class State:
         _check(_lib.sv_create_on(tensor.data_ptr(), tensor.numel() * tensor.element_size(), n, dt, st,
                                  ctypes.byref(h)), "sv_create_on")
         return cls(n, dt, _handle=h, _keep=tensor)
+
+    def rebind(self, tensor, n: int, dtype):
+        """Points a from_tensor() handle at another caller-owned CUDA tensor."""
+        dt = DTYPES[dtype]
+        _check(_lib.sv_rebind(self._h, tensor.data_ptr(), tensor.numel() * tensor.element_size(), n, dt),
+               "sv_rebind")
+        self.n, self.dt, self._keep = n, dt, tensor
+        return self
 
     def close(self):
         if getattr(self, "_h", None):
@@ -296,15 +308,29 @@ def batch_run(items, opts=None):
     return outs, list(st)[: len(items)]
 
 
+def batch_arena_bytes(items, opts=None) -> int:
+    arr, _keep, _outs = _batch_items(items)
+    b = _sz()
+    _check(_lib.sv_batch_arena_bytes(arr, len(items), _opts_ptr(opts), ctypes.byref(b)), "sv_batch_arena_bytes")
+    return int(b.value)
+
+
 class Batch:
     """A prepared batch (sv_batch_create): its CUDA graph is replayed by
     execute(); outputs are refreshed in place on every execute()."""
 
-    def __init__(self, items, opts=None):
+    def __init__(self, items, opts=None, arena=None):
+        """arena: optional caller-owned CUDA uint8 tensor of at least
+        arena_bytes(items) bytes (kept alive by the Batch)."""
         self._arr, self._keep, self.outputs = _batch_items(items)
+        self._arena = arena
         st = (ctypes.c_int * max(1, len(items)))()
         h = _vp()
-        rc = _lib.sv_batch_create(self._arr, len(items), _opts_ptr(opts), st, ctypes.byref(h))
+        if arena is None:
+            rc = _lib.sv_batch_create(self._arr, len(items), _opts_ptr(opts), st, ctypes.byref(h))
+        else:
+            rc = _lib.sv_batch_create_in(self._arr, len(items), _opts_ptr(opts), st, arena.data_ptr(),
+                                         arena.numel() * arena.element_size(), ctypes.byref(h))
         self.status = list(st)[: len(items)]
         _check(rc, "sv_batch_create")
         self._h = h
