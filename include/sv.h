@@ -72,6 +72,8 @@ typedef struct {
  *                    the FP32 units (error-free TwoProd / TwoSum transforms,
  *                    Dekker 1971; Joldes, Muller, Popescu 2017), about 47
  *                    significant bits per operation.
+ *   SV_ARITH_AUTO:   SV_ARITH_DF64 (on GB300 the FP64 pipe runs at about
+ *                    1/70 of the FP32 pipe).
  * complex64 states always compute in float32. */
 typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_NATIVE = 1, SV_ARITH_DF64 = 2 } sv_arith;
 
@@ -172,6 +174,8 @@ typedef struct {
     double  kernel_ms;       /* sum of kernel durations (opts->timing only) */
     double  max_kernel_ms;   /* longest single launch (opts->timing only)   */
     double  upload_bytes;    /* descriptors + coefficients copied host->device */
+    double  alu_ops;         /* modelled ALU lane operations of the passes:
+                                FP32 ops (complex64, df64) or FP64 ops (native) */
 } sv_apply_stats;
 int sv_last_stats(const sv_state* s, sv_apply_stats* out);
 

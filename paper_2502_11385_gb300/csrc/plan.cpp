@@ -237,11 +237,11 @@ static double block_instr(const Block& b, int arith) {
     return (arith == AK_DF64 ? 44.0 : 4.0) * D;
 }
 
-double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops) {
+double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops, double* alu_ops) {
     const double dim = std::ldexp(1.0, p.n);
     const double state = dim * amp_bytes;
     const double rate = arith == AK_FP64 ? mc.fp64_ips : mc.fp32_ips;
-    double total = 0, fl_all = 0;
+    double total = 0, fl_all = 0, ops_all = 0;
     for (const auto& ps : p.passes) {
         double fl = 0, instr = 0, smem = 0;
         for (int bi : ps.blocks) {
@@ -251,12 +251,14 @@ double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, do
         }
         if (arith == AK_DF64) instr += 60.0 * dim;  // float64 <-> double-float conversions per pass
         fl_all += fl;
+        ops_all += instr;
         const double alu = instr / rate;
         const double hbm = 2.0 * state / mc.hbm_Bps;
         const double sm = smem / mc.smem_Bps;
         total += std::max(std::max(alu, hbm), sm) + mc.launch_s;
     }
     if (flops) *flops = fl_all;
+    if (alu_ops) *alu_ops = ops_all;
     return total;
 }
 
@@ -287,9 +289,10 @@ Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int c
         if (p.model_s < best.model_s) best = std::move(p);
     }
     finalize(best.blocks, g);
-    double fl = 0;
-    best.model_s = model_cost(best, amp_bytes, arith, mc, &fl);
+    double fl = 0, ops = 0;
+    best.model_s = model_cost(best, amp_bytes, arith, mc, &fl, &ops);
     best.flops = fl;
+    best.alu_ops = ops;
     return best;
 }
 

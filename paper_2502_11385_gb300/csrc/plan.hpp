@@ -54,6 +54,7 @@ struct Plan {
     std::vector<Block> blocks;
     std::vector<Pass> passes;
     double flops = 0;      // modelled real flops (FMA = 2)
+    double alu_ops = 0;    // modelled ALU lane operations (FP32 for df64/complex64, FP64 native)
     double model_s = 0;    // modelled time
 };
 
@@ -83,7 +84,8 @@ std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, 
 
 // Modelled cost of a plan (seconds) for a state of `amp_bytes` per amplitude;
 // *flops receives the real flops of the block products (FMA = 2).
-double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops);
+double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops,
+                  double* alu_ops = nullptr);
 
 // Full planning with optional autotuning over fuse_k (0 = auto).
 Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int coalesce,

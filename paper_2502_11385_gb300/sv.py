@@ -42,7 +42,7 @@ class ApplyStats(ctypes.Structure):
                 ("tile_qubits", ctypes.c_int32), ("arith", ctypes.c_int32), ("n_launches", ctypes.c_int32),
                 ("flops", ctypes.c_double), ("hbm_bytes", ctypes.c_double), ("plan_ms", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("max_kernel_ms", ctypes.c_double),
-                ("upload_bytes", ctypes.c_double)]
+                ("upload_bytes", ctypes.c_double), ("alu_ops", ctypes.c_double)]
 
 
 class BatchItem(ctypes.Structure):
