@@ -151,6 +151,26 @@ int sv_probabilities(sv_state* s, double* out, size_t out_len, int out_is_device
 int sv_marginal_probabilities(sv_state* s, uint64_t qubit_mask, double* out,
                               size_t out_len, int out_is_device);
 
+/* Marginal distribution as sv_marginal_probabilities, for callers that cannot
+ * let a library allocate device memory: processes whose device memory is
+ * fully reserved by another allocator, and latency-critical loops where a
+ * cudaFree (which waits for the whole device) would stall other streams.  The
+ * paper has no counterpart; this is an interface convenience.
+ *   amplitudes: the state's device pointer (16-byte aligned, 2^n amplitudes
+ *               of dtype dt), read only; no handle is needed.
+ *   out:        2^popcount(mask) float64, host memory unless out_is_device.
+ *   cuda_stream: the cudaStream_t to run on (NULL = legacy default stream);
+ *               the call returns after the result is in out.
+ * It allocates nothing: its scratch is a static 1.5 MiB device array inside
+ * the library (held on every GPU that loads the library until exit), so the
+ * mask may select at most 16 qubits (SV_ERR_SIZE beyond).  The first call on
+ * each device looks the array up (with that device current); make that first
+ * call before any stream capture.  All calls share the array and clear what
+ * they use, so calls that overlap on the GPU race: serialise them. */
+int sv_marginal_probabilities_noalloc(const void* amplitudes, int n_qubits, int dt,
+                                      uint64_t qubit_mask, double* out, size_t out_len,
+                                      int out_is_device, void* cuda_stream);
+
 /* Copies the amplitudes (sv_state_bytes bytes, in the state's dtype) out, or
  * in (sv_set_amplitudes: checkpoint restore). */
 int sv_amplitudes(sv_state* s, void* out, size_t bytes, int out_is_device);

@@ -73,6 +73,7 @@ _SIGS = {
     "sv_apply_circuit": ([_vp, _vp, _sz, ctypes.POINTER(RunOpts)], _i32),
     "sv_probabilities": ([_vp, _dp, _sz, _i32], _i32),
     "sv_marginal_probabilities": ([_vp, _u64, _dp, _sz, _i32], _i32),
+    "sv_marginal_probabilities_noalloc": ([_vp, _i32, _i32, _u64, _dp, _sz, _i32, _vp], _i32),
     "sv_amplitudes": ([_vp, _vp, _sz, _i32], _i32),
     "sv_set_amplitudes": ([_vp, _vp, _sz, _i32], _i32),
     "sv_norm": ([_vp, ctypes.POINTER(ctypes.c_double)], _i32),
@@ -270,6 +271,21 @@ class State:
         v = ctypes.c_double()
         _check(_lib.sv_norm(self._h, ctypes.byref(v)), "sv_norm")
         return v.value
+
+
+def marginal_probabilities_noalloc(amplitudes_ptr: int, n: int, dtype, qubit_mask: int, out=None, stream=None):
+    """Marginal distribution read straight from a state's device pointer,
+    without allocating anything (sv_marginal_probabilities_noalloc): for
+    callers that cannot have device memory allocated for them.  At most 16
+    qubits in the mask; calls must not overlap on the GPU."""
+    nb = 1 << bin(qubit_mask).count("1")
+    if out is None:
+        out = np.empty(nb, dtype=np.float64)
+    p, dev, nbytes = _ptr_of(out)
+    _check(_lib.sv_marginal_probabilities_noalloc(amplitudes_ptr, n, DTYPES[dtype], qubit_mask, p,
+                                                  _f64_len(out, nbytes), dev, stream),
+           "sv_marginal_probabilities_noalloc")
+    return out
 
 
 def create(n: int, dtype="c128") -> State:
