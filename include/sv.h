@@ -252,6 +252,28 @@ typedef struct {
 } sv_batch_info;
 int sv_batch_stats(const sv_batch* b, sv_batch_info* out);
 
+/* CutQC reconstruction of the uncut distribution from the subcircuit-variant
+ * probabilities (Sec. III-A, Eqs. 3.2-3.7; the Builder's reconstruction, with
+ * its partial mode over chosen qubits, Sec. IV-A "Builder and Verifier").
+ *   up_probs:   3^K device pointers: the upstream circuit's distribution over
+ *               its width_a qubits for measurement variant v = sum_j m_j 3^j
+ *               (m_j: 0 = I/Z, 1 = X, 2 = Y on cut j).
+ *   down_probs: 4^K device pointers: the downstream distribution over its
+ *               width_b qubits for initialisation s = sum_j s_j 4^j
+ *               (s_j: 0 = |0>, 1 = |1>, 2 = |+>, 3 = |+i> on cut j).
+ *   cut_pos_a:  K upstream qubit indices of the cut wires.
+ *   keep_mask_a / keep_mask_b: qubits kept in the output (upstream mask must
+ *               exclude the cut qubits); the rest are summed out.
+ *   out:        2^(kept_a + kept_b) float64; index = kept upstream bits
+ *               (ascending) then kept downstream bits above them.
+ * Term sums are exact (signed 128-bit fixed point); 1 <= K <= 6.  The pointer
+ * tables are host arrays; the call allocates device scratch and returns after
+ * the result is in out. */
+int sv_cut_reconstruct(const double* const* up_probs, const double* const* down_probs,
+                       int n_cuts, int width_a, const int32_t* cut_pos_a, int width_b,
+                       uint64_t keep_mask_a, uint64_t keep_mask_b,
+                       double* out, size_t out_len, int out_is_device);
+
 /* Static description of a status code. */
 const char* sv_status_str(int status);
 

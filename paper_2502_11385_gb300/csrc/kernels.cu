@@ -31,6 +31,8 @@ __device__ __forceinline__ double fmaT(double a, double b, double c) { return fm
 // Shared-memory layout of a tile: 16-byte slots, XOR-swizzled so that warps
 // gathering amplitudes at power-of-two strides spread over the banks.
 // ---------------------------------------------------------------------------
+// swz(j) = j ^ L(j) with L linear over GF(2) (shifts and XORs), so
+// swz(a ^ b) = swz(a) ^ swz(b).
 template <typename R>
 __device__ __forceinline__ int swz(int j) {
     constexpr int VS = (sizeof(R) == 4) ? 1 : 0;  // log2(amplitudes per 16-byte slot); R = float or double
@@ -109,6 +111,13 @@ __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, cons
         pos[j] = op.pos[j];
         pm[j] = 1 << pos[j];
     }
+    // the swizzle is linear over GF(2) and base / offset bits are disjoint:
+    // swz(base | off) = swz(base) ^ swz(off)
+    constexpr int DS = K <= 4 ? D : 1;  // 5-qubit blocks recompute offsets (registers)
+    int soff[DS];
+#pragma unroll
+    for (int b = 0; b < DS; b++) soff[b] = swz<R>(group_offset<K>(b, pm));
+    auto sofs = [&](int b) { return K <= 4 ? soff[b & (DS - 1)] : swz<R>(group_offset<K>(b, pm)); };
     const int ng = 1 << (m - K);
     for (int g0 = threadIdx.x; g0 < ng; g0 += blockDim.x * G) {
         int base[G];
@@ -118,9 +127,9 @@ __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, cons
         for (int q = 0; q < G; q++) {
             const int g = g0 + q * blockDim.x;
             ok[q] = g < ng;
-            base[q] = insert_zero_bits<K>(ok[q] ? g : 0, pos);
+            base[q] = swz<R>(insert_zero_bits<K>(ok[q] ? g : 0, pos));
 #pragma unroll
-            for (int b = 0; b < D; b++) a[q][b] = sm[swz<R>(base[q] | group_offset<K>(b, pm))];
+            for (int b = 0; b < D; b++) a[q][b] = sm[base[q] ^ sofs(b)];
         }
 #pragma unroll(K <= 2 ? D : 1)
         for (int r = 0; r < D; r++) {
@@ -138,46 +147,78 @@ __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, cons
                     im[q] = fmaT(u.im, a[q][c].re, im[q]);
                 }
             }
-            const int off = group_offset<K>(r, pm);
+            const int off = sofs(r);
 #pragma unroll
             for (int q = 0; q < G; q++)
-                if (ok[q]) sm[swz<R>(base[q] | off)] = Cx<R>{re[q], im[q]};
+                if (ok[q]) sm[base[q] ^ off] = Cx<R>{re[q], im[q]};
         }
     }
+}
+
+// Diagonal ops visit amplitude i = threadIdx.x + it * kTileThreads.  The
+// phase-table index takes bit j from tile position pos[j] (or, for a
+// non-local qubit, from the tile's base index); the bits below log2 of the
+// CTA size come from the thread id and are gathered once per op.
+struct DiagIndex {
+    int idx_t;      // table-index bits fixed for this thread
+    int hp[5], hb[5];  // high tile positions (relative to the CTA size) and their table bits
+    int nh;
+    int sw_t;       // swizzle of the thread's part of i
+};
+
+template <typename SwzT>
+__device__ __forceinline__ DiagIndex diag_index(const DevOp& op, uint64_t tile_base) {
+    constexpr int LT = 8;  // log2(kTileThreads)
+    static_assert((1 << LT) == kTileThreads, "diag index split assumes 256 threads");
+    DiagIndex d;
+    d.idx_t = 0;
+    d.nh = 0;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        d.hp[j] = 0;
+        d.hb[j] = 0;
+        if (j < op.k) {
+            const int p = op.pos[j];
+            if (p < 0) d.idx_t |= (int)((tile_base >> op.qbit[j]) & 1) << j;
+            else if (p < LT) d.idx_t |= ((t >> p) & 1) << j;
+            else {
+                d.hp[d.nh] = p - LT;
+                d.hb[d.nh] = j;
+                d.nh++;
+            }
+        }
+    }
+    d.sw_t = swz<SwzT>(t);
+    return d;
+}
+
+template <typename SwzT>
+__device__ __forceinline__ void diag_at(const DiagIndex& d, int it, int& idx, int& sidx) {
+    idx = d.idx_t;
+#pragma unroll
+    for (int j = 0; j < 5; j++)
+        if (j < d.nh) idx |= ((it >> d.hp[j]) & 1) << d.hb[j];
+    sidx = d.sw_t ^ swz<SwzT>(it << 8);
 }
 
 template <typename R>
 __device__ __forceinline__ void op_diag(Cx<R>* sm, int m, const DevOp& op, const Cx<R>* __restrict__ M,
                                         uint64_t tile_base) {
-    int cidx = 0, lp[5], lb[5], nl = 0;
-#pragma unroll
-    for (int j = 0; j < 5; j++) {
-        if (j < op.k) {
-            if (op.pos[j] < 0) {
-                cidx |= (int)((tile_base >> op.qbit[j]) & 1) << j;
-            } else {
-                lp[nl] = op.pos[j];
-                lb[nl] = j;
-                nl++;
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 5; j++)
-        if (j >= nl) { lp[j] = 0; lb[j] = 31; }  // contributes nothing (bit shifted out)
+    const DiagIndex d = diag_index<R>(op, tile_base);
     const int N = 1 << m;
+    const int iters = (N + 255) >> 8;  // tiles smaller than the CTA: threads past N idle
     const bool sign_only = op.flags & OPF_SIGN_ONLY;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        int idx = cidx;
-#pragma unroll
-        for (int j = 0; j < 5; j++) idx |= (lb[j] < 31) ? (((i >> lp[j]) & 1) << lb[j]) : 0;
+    for (int it = 0; it < iters; it++) {
+        if ((int)threadIdx.x + (it << 8) >= N) break;
+        int idx, si;
+        diag_at<R>(d, it, idx, si);
         const Cx<R> u = M[idx];
-        const int s = swz<R>(i);
-        Cx<R> a = sm[s];
+        const Cx<R> a = sm[si];
         if (sign_only) {
-            if (u.re < R(0)) sm[s] = Cx<R>{-a.re, -a.im};
+            if (u.re < R(0)) sm[si] = Cx<R>{-a.re, -a.im};
         } else {
-            sm[s] = Cx<R>{fmaT(u.re, a.re, -u.im * a.im), fmaT(u.re, a.im, u.im * a.re)};
+            sm[si] = Cx<R>{fmaT(u.re, a.re, -u.im * a.im), fmaT(u.re, a.im, u.im * a.re)};
         }
     }
 }
@@ -296,9 +337,9 @@ __device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, con
         for (int q = 0; q < G; q++) {
             const int g = g0 + q * blockDim.x;
             ok[q] = g < ng;
-            base[q] = insert_zero_bits<K>(ok[q] ? g : 0, pos);
+            base[q] = swz<double>(insert_zero_bits<K>(ok[q] ? g : 0, pos));
 #pragma unroll
-            for (int b = 0; b < D; b++) a[q][b] = sm[swz<double>(base[q] | group_offset<K>(b, pm))];
+            for (int b = 0; b < D; b++) a[q][b] = sm[base[q] ^ swz<double>(group_offset<K>(b, pm))];
         }
 #pragma unroll(K <= 1 ? D : 1)
         for (int r = 0; r < D; r++) {
@@ -325,12 +366,12 @@ __device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, con
                     df_mac(ih[q], il[q], u.ih, u.il, a[q][c].rh, a[q][c].rl);
                 }
             }
-            const int off = group_offset<K>(r, pm);
+            const int off = swz<double>(group_offset<K>(r, pm));
 #pragma unroll
             for (int q = 0; q < G; q++) {
                 df_norm(rh[q], rl[q]);
                 df_norm(ih[q], il[q]);
-                if (ok[q]) sm[swz<double>(base[q] | off)] = DF4{rh[q], rl[q], ih[q], il[q]};
+                if (ok[q]) sm[base[q] ^ off] = DF4{rh[q], rl[q], ih[q], il[q]};
             }
         }
     }
@@ -338,42 +379,27 @@ __device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, con
 
 __device__ __forceinline__ void op_diag_df(DF4* sm, int m, const DevOp& op, const DF4* __restrict__ M,
                                            uint64_t tile_base) {
-    int cidx = 0, lp[5], lb[5], nl = 0;
-#pragma unroll
-    for (int j = 0; j < 5; j++) {
-        if (j < op.k) {
-            if (op.pos[j] < 0) {
-                cidx |= (int)((tile_base >> op.qbit[j]) & 1) << j;
-            } else {
-                lp[nl] = op.pos[j];
-                lb[nl] = j;
-                nl++;
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 5; j++)
-        if (j >= nl) { lp[j] = 0; lb[j] = 31; }
+    const DiagIndex d = diag_index<double>(op, tile_base);
     const int N = 1 << m;
+    const int iters = (N + 255) >> 8;  // tiles smaller than the CTA: threads past N idle
     const bool sign_only = op.flags & OPF_SIGN_ONLY;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        int idx = cidx;
-#pragma unroll
-        for (int j = 0; j < 5; j++) idx |= (lb[j] < 31) ? (((i >> lp[j]) & 1) << lb[j]) : 0;
+    for (int it = 0; it < iters; it++) {
+        if ((int)threadIdx.x + (it << 8) >= N) break;
+        int idx, si;
+        diag_at<double>(d, it, idx, si);
         const DF4 u = M[idx];
-        const int s = swz<double>(i);
-        const DF4 a = sm[s];
+        const DF4 a = sm[si];
         if (sign_only) {
-            if (u.rh < 0.f) sm[s] = DF4{-a.rh, -a.rl, -a.ih, -a.il};
+            if (u.rh < 0.f) sm[si] = DF4{-a.rh, -a.rl, -a.ih, -a.il};
         } else {
-            float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-            df_mac(rh, rl, u.rh, u.rl, a.rh, a.rl);
+            float rh, rl, ih, il;
+            df_mul(rh, rl, u.rh, u.rl, a.rh, a.rl);
             df_mac(rh, rl, -u.ih, -u.il, a.ih, a.il);
-            df_mac(ih, il, u.rh, u.rl, a.ih, a.il);
+            df_mul(ih, il, u.rh, u.rl, a.ih, a.il);
             df_mac(ih, il, u.ih, u.il, a.rh, a.rl);
             df_norm(rh, rl);
             df_norm(ih, il);
-            sm[s] = DF4{rh, rl, ih, il};
+            sm[si] = DF4{rh, rl, ih, il};
         }
     }
 }

@@ -88,6 +88,8 @@ _SIGS = {
     "sv_rebind": ([_vp, _vp, _sz, _i32, _i32], _i32),
     "sv_batch_destroy": ([_vp], None),
     "sv_batch_stats": ([_vp, ctypes.POINTER(BatchInfo)], _i32),
+    "sv_cut_reconstruct": ([ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _i32, ctypes.POINTER(ctypes.c_int32),
+                            _i32, _u64, _u64, _dp, _sz, _i32], _i32),
     "sv_status_str": ([_i32], ctypes.c_char_p),
     "sv_version": ([], ctypes.c_char_p),
     "sv_plan_build": ([_i32, _i32, _vp, _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(_vp)], _i32),
@@ -376,6 +378,29 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def cut_reconstruct(up_probs, down_probs, width_a, cut_pos, width_b, keep_mask_a=None, keep_mask_b=None,
+                    out=None):
+    """CutQC reconstruction from device-resident variant distributions
+    (torch CUDA tensors of float64): up_probs has 3^K entries, down_probs 4^K.
+    Returns the distribution over the kept qubits (kept upstream qubits first)."""
+    K = len(cut_pos)
+    if keep_mask_a is None:
+        keep_mask_a = ((1 << width_a) - 1) & ~sum(1 << q for q in cut_pos)
+    if keep_mask_b is None:
+        keep_mask_b = (1 << width_b) - 1
+    na = bin(keep_mask_a).count("1")
+    nb = bin(keep_mask_b).count("1")
+    if out is None:
+        out = np.empty(1 << (na + nb), dtype=np.float64)
+    ups = (_vp * len(up_probs))(*[t.data_ptr() for t in up_probs])
+    downs = (_vp * len(down_probs))(*[t.data_ptr() for t in down_probs])
+    cp = (ctypes.c_int32 * K)(*cut_pos)
+    p, dev, nbytes = _ptr_of(out)
+    _check(_lib.sv_cut_reconstruct(ups, downs, K, width_a, cp, width_b, keep_mask_a, keep_mask_b, p,
+                                   _f64_len(out, nbytes), dev), "sv_cut_reconstruct")
+    return out
 
 
 class Plan:

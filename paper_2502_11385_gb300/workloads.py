@@ -377,3 +377,144 @@ def serving_stream(count: int, rate: float, seed: int = 5, wmin=10, wmax=30,
             g = qaoa(w, max(1, d // 5), sub)[0]
         out.append(Request(i, t, w, dt, fam, d, g))
     return out
+
+
+# ---------------------------------------------------------------------------
+# The paper's benchmark families (Sec. V-B), as generators written from their
+# defining papers onto this gate set.  T^dagger = U3(0, 0, -pi/4); sqrt(X),
+# sqrt(Y) are RX(pi/2), RY(pi/2) (equal up to a global phase).
+# ---------------------------------------------------------------------------
+def _tdg(q):
+    return (U3, q, -1, 0.0, 0.0, -math.pi / 4)
+
+
+def toffoli(a: int, b: int, t: int):
+    """CCX(a, b -> t) from H, T, T^dagger and six CX (the standard exact
+    Clifford+T decomposition)."""
+    return [(H, t, -1), (CX, b, t), _tdg(t), (CX, a, t), (T, t, -1), (CX, b, t), _tdg(t), (CX, a, t),
+            (T, b, -1), (T, t, -1), (H, t, -1), (CX, a, b), (T, a, -1), _tdg(b), (CX, a, b)]
+
+
+def cuccaro_adder(m: int, a_val: int = None, b_val: int = None):
+    """Ripple-carry adder of Cuccaro, Draper, Kutin and Moulton (2004) on two
+    m-bit registers with one ancilla and a carry-out: 2m + 2 qubits.
+    Layout: qubit 0 = carry-in ancilla c, qubits 1 + 2i = a_i, 2 + 2i = b_i,
+    qubit 2m + 1 = carry-out z.  Computes b <- a + b (mod 2^m), z <- carry.
+    MAJ(c, b, a) = CX(a, b) CX(a, c) CCX(c, b -> a);
+    UMA(c, b, a) = CCX(c, b -> a) CX(a, c) CX(c, b).
+    Optional a_val / b_val prepend X gates that load basis inputs."""
+    n = 2 * m + 2
+    A = lambda i: 1 + 2 * i
+    B = lambda i: 2 + 2 * i
+    rows = []
+    if a_val is not None:
+        rows += [(X, A(i), -1) for i in range(m) if (a_val >> i) & 1]
+    if b_val is not None:
+        rows += [(X, B(i), -1) for i in range(m) if (b_val >> i) & 1]
+
+    def maj(c, b, a):
+        return [(CX, a, b), (CX, a, c)] + toffoli(c, b, a)
+
+    def uma(c, b, a):
+        return toffoli(c, b, a) + [(CX, a, c), (CX, c, b)]
+
+    carries = [0] + [A(i) for i in range(m - 1)]
+    for i in range(m):
+        rows += maj(carries[i], B(i), A(i))
+    rows.append((CX, A(m - 1), n - 1))
+    for i in range(m - 1, -1, -1):
+        rows += uma(carries[i], B(i), A(i))
+    return gates(rows)
+
+
+def adder_output_index(m: int, a_val: int, b_val: int) -> int:
+    """Basis index the adder maps |a, b> to: a unchanged, b = a + b mod 2^m,
+    carry-out set, ancilla back to 0."""
+    s = a_val + b_val
+    idx = 0
+    for i in range(m):
+        idx |= ((a_val >> i) & 1) << (1 + 2 * i)
+        idx |= ((s >> i) & 1) << (2 + 2 * i)
+    idx |= ((s >> m) & 1) << (2 * m + 1)
+    return idx
+
+
+def bernstein_vazirani(n: int, secret: int):
+    """Bernstein-Vazirani (1993): n - 1 data qubits (0..n-2) and an ancilla
+    (n-1) prepared in |->; the oracle CX(i, ancilla) for every set bit of the
+    secret; H on the data qubits reads the secret out with probability 1."""
+    anc = n - 1
+    rows = [(X, anc, -1), (H, anc, -1)] + [(H, q, -1) for q in range(n - 1)]
+    rows += [(CX, q, anc) for q in range(n - 1) if (secret >> q) & 1]
+    rows += [(H, q, -1) for q in range(n - 1)]
+    return gates(rows)
+
+
+def aqft(n: int, degree: int, j: int = 0):
+    """Approximate QFT (Barenco, Ekert, Suominen, Torma 1996) of the basis state
+    |j>: the QFT with only the controlled phases between qubits at distance
+    <= degree kept (degree >= n - 1 gives the exact QFT), then bit reversal."""
+    rows = [(X, q, -1) for q in range(n) if (j >> q) & 1]
+
+    def cp(phi, c, t):
+        return [(U3, c, -1, 0.0, 0.0, phi / 2), (CX, c, t),
+                (U3, t, -1, 0.0, 0.0, -phi / 2), (CX, c, t),
+                (U3, t, -1, 0.0, 0.0, phi / 2)]
+
+    for tq in range(n - 1, -1, -1):
+        rows.append((H, tq, -1))
+        for cq in range(tq - 1, -1, -1):
+            if tq - cq <= degree:
+                rows += cp(math.pi / (1 << (tq - cq)), cq, tq)
+    for q in range(n // 2):
+        rows.append((SWAP, q, n - 1 - q))
+    return gates(rows)
+
+
+def hwea(n: int, layers: int, seed: int):
+    """Hardware-efficient ansatz (Moll et al. 2018 style): per layer RY and RZ
+    on every qubit with seeded angles, then a CX ladder CX(q, q+1)."""
+    rng = SplitMix64(seed)
+    rows = []
+    for _ in range(layers):
+        for q in range(n):
+            rows.append((RY, q, -1, 2 * math.pi * rng.uniform()))
+            rows.append((RZ, q, -1, 2 * math.pi * rng.uniform()))
+        rows += [(CX, q, q + 1) for q in range(n - 1)]
+    return gates(rows)
+
+
+def supremacy(rows_: int, cols: int, cycles: int, seed: int):
+    """2-D random circuit in the style of Boixo et al. (2018) on a rows x cols
+    grid (qubit r*cols + c): H on every qubit, then per cycle CZ on one of
+    eight edge patterns (cycling horizontal / vertical, even / odd offsets)
+    and, on qubits outside this cycle's CZs, a seeded single-qubit gate from
+    {sqrt(X), sqrt(Y), T}, never repeating the qubit's previous one."""
+    rng = SplitMix64(seed)
+    n = rows_ * cols
+    q = lambda r, c: r * cols + c
+    out = [(H, i, -1) for i in range(n)]
+    last = [-1] * n
+    for cyc in range(cycles):
+        pat = cyc % 8
+        horiz = pat in (0, 1, 4, 5)
+        par, off = pat % 2, (pat // 2) % 2
+        edges = []
+        for r in range(rows_):
+            for c in range(cols):
+                if horiz and c + 1 < cols and (c % 2) == par and (r % 2) == off:
+                    edges.append((q(r, c), q(r, c + 1)))
+                if not horiz and r + 1 < rows_ and (r % 2) == par and (c % 2) == off:
+                    edges.append((q(r, c), q(r + 1, c)))
+        busy = set()
+        for a, b in edges:
+            out.append((CZ, a, b))
+            busy |= {a, b}
+        for i in range(n):
+            if i in busy:
+                continue
+            choices = [k for k in range(3) if k != last[i]]
+            k = choices[rng.below(len(choices))]
+            last[i] = k
+            out.append([(RX, i, -1, math.pi / 2), (RY, i, -1, math.pi / 2), (T, i, -1)][k])
+    return gates(out)

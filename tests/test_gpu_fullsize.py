@@ -118,3 +118,56 @@ def test_bench_workload_uudagger_c128(env):
     st.close()
     del buf
     torch.cuda.empty_cache()
+
+
+def test_adder_30q_exact_sum(env):
+    """Cuccaro adder, 14-bit registers (30 qubits, complex128): the basis input
+    |a, b> must end in the single basis state |a, a+b, carry>."""
+    torch, sv, free = env
+    m = 14
+    a, b = 12345, 9876
+    n = 2 * m + 2
+    buf, st = _state(torch, sv, n, "c128")
+    st.apply_circuit(W.cuccaro_adder(m, a, b))
+    p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    st.probabilities(p)
+    idx = W.adder_output_index(m, a, b)
+    assert abs(p[idx].item() - 1) <= 1e-10
+    assert abs(st.norm() - 1) <= 1e-10
+    st.close()
+    del buf, p
+    torch.cuda.empty_cache()
+
+
+def test_bernstein_vazirani_30q(env):
+    torch, sv, free = env
+    n = 30
+    secret = 0b10110011100011110000111110101
+    buf, st = _state(torch, sv, n, "c64")
+    st.apply_circuit(W.bernstein_vazirani(n, secret))
+    p = torch.empty(1 << n, dtype=torch.float64, device="cuda")
+    st.probabilities(p)
+    got = p[secret].item() + p[secret | (1 << (n - 1))].item()   # ancilla is |->
+    assert abs(got - 1) <= 1e-4
+    st.close()
+    del buf, p
+    torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_qft_30q_sampled_amplitudes(env, dtype):
+    """QFT of a basis state at 30 qubits: 65536 sampled amplitudes against the
+    closed form e^{2 pi i j k / 2^n} / 2^(n/2)."""
+    torch, sv, free = env
+    n, j = 30, 0x2345677
+    buf, st = _state(torch, sv, n, dtype)
+    st.apply_circuit(W.qft_basis(n, j))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    k = np.sort(rng.choice(1 << n, size=65536, replace=False))
+    got = buf[torch.from_numpy(k).cuda()].cpu().numpy().astype(np.complex128)
+    ref = np.exp(2j * np.pi * ((j * k) % (1 << n)) / (1 << n)) / 2 ** (n / 2)
+    assert np.abs(got - ref).max() <= (1e-12 if dtype == "c128" else 1e-5)
+    st.close()
+    del buf
+    torch.cuda.empty_cache()

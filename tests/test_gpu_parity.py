@@ -335,3 +335,31 @@ def test_cut_variants_batched(sv):
     assert all(s == 0 for s in status)
     for (n, dt, g, _), o in zip(items, outs):
         assert np.abs(o - oracle.probabilities(oracle.run(n, g))).max() <= 4 * TOL[dt]
+
+
+# ---------------------------------------------------------------------------
+# cut reconstruction (Sec. III-A, Eqs. 3.2-3.7)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,depth,cut_lo,k,switch", [(6, 4, 2, 1, 2), (10, 6, 4, 3, 3), (12, 6, 5, 2, 3)])
+def test_cut_reconstruction_on_gpu(sv, n, depth, cut_lo, k, switch):
+    import torch
+    from oracle import cut
+    cc = W.cuttable_brickwork(n, depth, 300 + n, cut_lo=cut_lo, n_cuts=k, switch_layer=switch)
+    ups, downs = cc.upstream_variants(), cc.downstream_variants()
+    up_t = [torch.empty(1 << cc.width_a, dtype=torch.float64, device="cuda") for _ in ups]
+    dn_t = [torch.empty(1 << cc.width_b, dtype=torch.float64, device="cuda") for _ in downs]
+    items = [(cc.width_a, "c128", g, t) for g, t in zip(ups, up_t)] + \
+            [(cc.width_b, "c128", g, t) for g, t in zip(downs, dn_t)]
+    _, status = sv.batch_run(items)
+    assert all(s == 0 for s in status)
+    rec = sv.cut_reconstruct(up_t, dn_t, cc.width_a, list(cc.cut_qubits), cc.width_b)
+    full = oracle.probabilities(oracle.run(n, cc.full))
+    assert np.abs(rec - full).max() <= 1e-12
+    p_up = [t.cpu().numpy() for t in up_t]
+    p_dn = [t.cpu().numpy() for t in dn_t]
+    assert np.abs(rec - cut.reconstruct(p_up, p_dn, cc.width_a, list(cc.cut_qubits))).max() <= 1e-13
+    # partial reconstruction over chosen qubits: upstream qubit 0 and the last downstream qubit
+    ka, kb = 0b1, 1 << (cc.width_b - 1)
+    part = sv.cut_reconstruct(up_t, dn_t, cc.width_a, list(cc.cut_qubits), cc.width_b, ka, kb)
+    gmask = 1 | (1 << (n - 1))   # the same two qubits in the uncut circuit
+    assert np.abs(part - oracle.marginal(oracle.run(n, cc.full), gmask)).max() <= 1e-12
