@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--form", default="full", choices=["full", "batch", "serve"],
+                    help="full: one circuit (default); batch: the 91 cut-subcircuit variants of the "
+                         "40-qubit brickwork; serve: a Poisson request stream")
+    ap.add_argument("--serve-count", type=int, default=2000)
+    ap.add_argument("--serve-wmax", type=int, default=30)
     return ap.parse_args()
 
 
@@ -194,10 +199,107 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_form(args):
+    """Batched form: all 4^3 downstream (22 q) and 3^3 upstream (21 q) variants
+    of the 40-qubit cuttable brickwork (depth 12, seed 4) in one prepared batch
+    (CUDA-graph replay), against looping the single-circuit path over the same
+    variants on the same GPU.  Both write every variant's probabilities to
+    device memory; results are compared bitwise."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2502_11385_gb300 import sv, workloads as W
+    cc = W.workload_cut40()
+    ups, downs = cc.upstream_variants(), cc.downstream_variants()
+    out = {"form": "batch", "metric": "cut-subcircuit variants/s", "unit": "variants/s",
+           "config": {"workload": "40q cuttable brickwork depth 12 seed 4, 3 cuts: 27 x 21q + 64 x 22q variants"},
+           "results": []}
+    for dtype in ("c128", "c64"):
+        outs = [torch.empty(1 << cc.width_a, dtype=torch.float64, device="cuda") for _ in ups]
+        outs += [torch.empty(1 << cc.width_b, dtype=torch.float64, device="cuda") for _ in downs]
+        gl = ups + downs
+        widths = [cc.width_a] * len(ups) + [cc.width_b] * len(downs)
+        items = [(w, dtype, g, o) for w, g, o in zip(widths, gl, outs)]
+        t0 = time.perf_counter()
+        b = sv.Batch(items)
+        build_ms = (time.perf_counter() - t0) * 1e3
+        for _ in range(args.warmup):
+            b.execute()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            b.execute()
+        torch.cuda.synchronize()
+        batch_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        ref = [o.clone() for o in outs]
+        info = b.stats()
+        b.close()
+        # loop of the single-circuit path
+        ctype = torch.complex128 if dtype == "c128" else torch.complex64
+        bufs = {w: torch.empty(1 << w, dtype=ctype, device="cuda") for w in set(widths)}
+        stream = torch.cuda.Stream()
+        h = sv.State.from_tensor(bufs[cc.width_a], cc.width_a, dtype, stream=stream.cuda_stream)
+
+        def loop():
+            for w, g, o in zip(widths, gl, outs):
+                h.rebind(bufs[w], w, dtype)
+                h.reset(0)
+                h.apply_circuit(g)
+                h.probabilities(o)
+        for _ in range(max(1, args.warmup // 2)):
+            loop()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            loop()
+        torch.cuda.synchronize()
+        loop_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        same = all(torch.equal(a, c) for a, c in zip(ref, outs))
+        h.close()
+        del bufs
+        nv = len(items)
+        out["results"].append({"dtype": dtype, "variants": nv, "batched_ms": round(batch_ms, 3),
+                               "loop_ms": round(loop_ms, 3), "batched_variants_per_s": round(nv / batch_ms * 1e3, 2),
+                               "loop_variants_per_s": round(nv / loop_ms * 1e3, 2),
+                               "speedup": round(loop_ms / batch_ms, 3), "bitwise_equal": same,
+                               "graph_launches": info["n_launches"], "arena_gib": round(info["arena_bytes"] / 2**30, 3),
+                               "batch_build_ms": round(build_ms, 1)})
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+
+
+def run_serve_form(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2502_11385_gb300 import serve, sv, workloads as W
+    opts = sv.run_opts()
+    probe = W.serving_stream(100, 1.0, seed=1005, wmin=10, wmax=args.serve_wmax)
+    serve.mean_service_time(probe[:10], opts)
+    sbar = serve.mean_service_time(probe, opts)
+    out = {"form": "serve", "metric": "circuits/s, p50/p99 latency", "mean_service_s": round(sbar, 5),
+           "config": {"workload": f"Poisson stream of {args.serve_count} requests, width log-uniform 10-"
+                                  f"{args.serve_wmax}, depth 5-40, brickwork/QAOA 50/50, c64/c128 50/50, seed 5"},
+           "runs": []}
+    for rho in (0.7, 2.0):
+        reqs = W.serving_stream(args.serve_count, rho / sbar, seed=5, wmin=10, wmax=args.serve_wmax)
+        srv = serve.Server(opts=opts, keep_outputs=False)
+        _, st = srv.run(reqs)
+        _, ss = serve.run_serial(reqs, opts, keep_outputs=False)
+        out["runs"].append({"rho": rho, "rate_per_s": round(rho / sbar, 3), "served": st, "serial": ss})
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.form == "batch":
+        run_batch_form(args)
+        return
+    if args.form == "serve":
+        run_serve_form(args)
         return
     import numpy as np
     import torch

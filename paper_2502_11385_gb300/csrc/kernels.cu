@@ -131,14 +131,32 @@ __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, cons
 #pragma unroll
             for (int b = 0; b < D; b++) a[q][b] = sm[base[q] ^ sofs(b)];
         }
+        // for blocks of up to 3 qubits the coefficient rows are
+        // software-pipelined: row r + 1 is loaded while row r is multiplied
+        constexpr bool kPipe = K <= 3 && sizeof(R) == 4;  // FP64 is bound by its pipe anyway
+        constexpr int DP = kPipe ? D : 1;
+        Cx<R> un[DP];
+        if constexpr (kPipe) {
+#pragma unroll
+            for (int c = 0; c < D; c++) un[c] = M[c];
+        }
 #pragma unroll(K <= 2 ? D : 1)
         for (int r = 0; r < D; r++) {
+            Cx<R> ur[DP];
+            if constexpr (kPipe) {
+#pragma unroll
+                for (int c = 0; c < D; c++) ur[c] = un[c];
+                if (r + 1 < D) {
+#pragma unroll
+                    for (int c = 0; c < D; c++) un[c] = M[(r + 1) * D + c];
+                }
+            }
             R re[G], im[G];
 #pragma unroll
             for (int q = 0; q < G; q++) re[q] = im[q] = R(0);
 #pragma unroll
             for (int c = 0; c < D; c++) {
-                const Cx<R> u = M[r * D + c];
+                const Cx<R> u = kPipe ? ur[c % DP] : M[r * D + c];
 #pragma unroll
                 for (int q = 0; q < G; q++) {
                     re[q] = fmaT(u.re, a[q][c].re, re[q]);
@@ -321,7 +339,7 @@ __device__ __forceinline__ void df_mul(float& sh, float& sl, float xh, float xl,
 template <int K>
 __device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, const DF4* __restrict__ M) {
     constexpr int D = 1 << K;
-    constexpr int G = K <= 2 ? 2 : 1;
+    constexpr int G = K <= 3 ? 2 : 1;
     int pos[K], pm[K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
