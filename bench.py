@@ -257,11 +257,27 @@ def run_batch_form(args):
         same = all(torch.equal(a, c) for a, c in zip(ref, outs))
         h.close()
         del bufs
+        # shared work: upstream body once, downstream by linearity (1 + 2^K bodies)
+        up_o = [torch.empty_like(o) for o in outs[:len(ups)]]
+        dn_o = [torch.empty_like(o) for o in outs[len(ups):]]
+        sv.cut_variants(cc, dtype, up_o, dn_o)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.cut_variants(cc, dtype, up_o, dn_o)
+        torch.cuda.synchronize()
+        shared_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        shared_err = max((a - c).abs().max().item() for a, c in zip(ref, up_o + dn_o))
+        del up_o, dn_o
         nv = len(items)
         out["results"].append({"dtype": dtype, "variants": nv, "batched_ms": round(batch_ms, 3),
                                "loop_ms": round(loop_ms, 3), "batched_variants_per_s": round(nv / batch_ms * 1e3, 2),
                                "loop_variants_per_s": round(nv / loop_ms * 1e3, 2),
                                "speedup": round(loop_ms / batch_ms, 3), "bitwise_equal": same,
+                               "shared_work_ms": round(shared_ms, 3),
+                               "shared_work_variants_per_s": round(nv / shared_ms * 1e3, 2),
+                               "shared_work_speedup_vs_loop": round(loop_ms / shared_ms, 3),
+                               "shared_work_max_abs_dp": shared_err,
                                "graph_launches": info["n_launches"], "arena_gib": round(info["arena_bytes"] / 2**30, 3),
                                "batch_build_ms": round(build_ms, 1)})
         torch.cuda.empty_cache()

@@ -274,6 +274,26 @@ int sv_cut_reconstruct(const double* const* up_probs, const double* const* down_
                        uint64_t keep_mask_a, uint64_t keep_mask_b,
                        double* out, size_t out_len, int out_is_device);
 
+/* Cut-subcircuit variants with shared work (the Evaluator's instances,
+ * Sec. IV-A, Fig. 1), producing the same outputs as running every variant
+ * through sv_batch_run, within the tolerance of the arithmetic:
+ *   upstream: body_a (width_a qubits) is simulated once from |0..0>; variant
+ *     v = sum_j m_j 3^j appends the basis change of cut j (m_j: 0 = I/Z none,
+ *     1 = X: H, 2 = Y: S^dagger then H) on qubit cut_pos_a[j] to a copy;
+ *     its probabilities go to up_out[v] (2^width_a float64).
+ *   downstream: body_b (width_b qubits) is simulated from each computational
+ *     basis state of the cut qubits cut_pos_b[] (2^K runs); variant
+ *     s = sum_j s_j 4^j (s_j: 0 = |0>, 1 = |1>, 2 = |+>, 3 = |+i>) is formed as
+ *     a linear combination of those states (the body is linear); its
+ *     probabilities go to down_out[s] (2^width_b float64).
+ * 1 + 2^K body simulations replace 3^K + 4^K.  Outputs are host memory
+ * unless outs_on_device; 1 <= K <= 6. */
+int sv_cut_variants(int dt, const sv_gate* body_a, size_t n_a, int width_a,
+                    const int32_t* cut_pos_a, const sv_gate* body_b, size_t n_b,
+                    int width_b, const int32_t* cut_pos_b, int n_cuts,
+                    double* const* up_out, double* const* down_out,
+                    int outs_on_device, const sv_run_opts* opts);
+
 /* Static description of a status code. */
 const char* sv_status_str(int status);
 

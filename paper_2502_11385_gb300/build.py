@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsv.so")
-SOURCES = ["plan.cpp", "kernels.cu", "api.cu", "noalloc.cu", "cut.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "api.cu", "noalloc.cu", "cut.cu", "variants.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

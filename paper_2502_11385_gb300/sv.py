@@ -90,6 +90,9 @@ _SIGS = {
     "sv_batch_stats": ([_vp, ctypes.POINTER(BatchInfo)], _i32),
     "sv_cut_reconstruct": ([ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32, _i32, ctypes.POINTER(ctypes.c_int32),
                             _i32, _u64, _u64, _dp, _sz, _i32], _i32),
+    "sv_cut_variants": ([_i32, _vp, _sz, _i32, ctypes.POINTER(ctypes.c_int32), _vp, _sz, _i32,
+                         ctypes.POINTER(ctypes.c_int32), _i32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32,
+                         ctypes.POINTER(RunOpts)], _i32),
     "sv_status_str": ([_i32], ctypes.c_char_p),
     "sv_version": ([], ctypes.c_char_p),
     "sv_plan_build": ([_i32, _i32, _vp, _sz, ctypes.POINTER(RunOpts), ctypes.POINTER(_vp)], _i32),
@@ -401,6 +404,26 @@ def cut_reconstruct(up_probs, down_probs, width_a, cut_pos, width_b, keep_mask_a
     _check(_lib.sv_cut_reconstruct(ups, downs, K, width_a, cp, width_b, keep_mask_a, keep_mask_b, p,
                                    _f64_len(out, nbytes), dev), "sv_cut_reconstruct")
     return out
+
+
+def cut_variants(cc, dtype="c128", up_out=None, down_out=None, opts=None):
+    """All cut-subcircuit variants of a workloads.CutCircuit with shared work
+    (sv_cut_variants).  Outputs: lists of 3^K and 4^K probability vectors
+    (numpy on the host, or caller-supplied CUDA tensors)."""
+    K = cc.n_cuts
+    ga, gb = as_gates(cc.body_a), as_gates(cc.body_b)
+    if up_out is None:
+        up_out = [np.empty(1 << cc.width_a) for _ in range(3 ** K)]
+    if down_out is None:
+        down_out = [np.empty(1 << cc.width_b) for _ in range(4 ** K)]
+    on_dev = 0 if isinstance(up_out[0], np.ndarray) else 1
+    ups = (_vp * len(up_out))(*[_ptr_of(o)[0] for o in up_out])
+    downs = (_vp * len(down_out))(*[_ptr_of(o)[0] for o in down_out])
+    ca = (ctypes.c_int32 * K)(*cc.cut_qubits)
+    cb = (ctypes.c_int32 * K)(*[q - cc.offset_b for q in cc.cut_qubits])
+    _check(_lib.sv_cut_variants(DTYPES[dtype], ga.ctypes.data, len(ga), cc.width_a, ca, gb.ctypes.data, len(gb),
+                                cc.width_b, cb, K, ups, downs, on_dev, _opts_ptr(opts)), "sv_cut_variants")
+    return up_out, down_out
 
 
 class Plan:

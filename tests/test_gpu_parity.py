@@ -363,3 +363,21 @@ def test_cut_reconstruction_on_gpu(sv, n, depth, cut_lo, k, switch):
     part = sv.cut_reconstruct(up_t, dn_t, cc.width_a, list(cc.cut_qubits), cc.width_b, ka, kb)
     gmask = 1 | (1 << (n - 1))   # the same two qubits in the uncut circuit
     assert np.abs(part - oracle.marginal(oracle.run(n, cc.full), gmask)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_cut_variants_shared_work_matches_plain(sv, dtype):
+    """Variant shortcuts (shared upstream body, downstream by linearity) give
+    the same distributions as simulating every variant on its own."""
+    cc = W.cuttable_brickwork(13, 6, 41, cut_lo=5, n_cuts=3, switch_layer=3)
+    up, down = sv.cut_variants(cc, dtype)
+    ups, downs = cc.upstream_variants(), cc.downstream_variants()
+    for g, p in zip(ups, up):
+        assert np.abs(p - oracle.probabilities(oracle.run(cc.width_a, g))).max() <= 4 * TOL[dtype]
+    for g, p in zip(downs, down):
+        assert np.abs(p - oracle.probabilities(oracle.run(cc.width_b, g))).max() <= 4 * TOL[dtype]
+    # and reconstruction from the shared-work variants gives the uncut circuit
+    if dtype == "c128":
+        from oracle import cut
+        rec = cut.reconstruct(up, down, cc.width_a, list(cc.cut_qubits))
+        assert np.abs(rec - oracle.probabilities(oracle.run(13, cc.full))).max() <= 1e-12
