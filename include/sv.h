@@ -72,10 +72,20 @@ typedef struct {
  *                    the FP32 units (error-free TwoProd / TwoSum transforms,
  *                    Dekker 1971; Joldes, Muller, Popescu 2017), about 47
  *                    significant bits per operation.
- *   SV_ARITH_AUTO:   SV_ARITH_DF64 (on GB300 the FP64 pipe runs at about
- *                    1/70 of the FP32 pipe).
+ *   SV_ARITH_TC:     float64 storage, the state held in Q62 fixed point in
+ *                    shared memory, block products on the tensor cores with
+ *                    an exact split into 7-bit digits (bfloat16 products,
+ *                    exact float32 level sums; error below 2^-51 per
+ *                    product); requires amplitude components of magnitude
+ *                    at most 1 (any normalised state).
+ *   SV_ARITH_AUTO:   SV_ARITH_TC for states of 8 or more qubits, else
+ *                    SV_ARITH_DF64 (on GB300 the FP64 pipe runs at about 1/70
+ *                    of the FP32 pipe).  Amplitudes supplied by the caller
+ *                    (sv_set_amplitudes, sv_create_on) are checked once:
+ *                    if a component exceeds 1 in magnitude the call uses
+ *                    SV_ARITH_DF64 instead.
  * complex64 states always compute in float32. */
-typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_NATIVE = 1, SV_ARITH_DF64 = 2 } sv_arith;
+typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_NATIVE = 1, SV_ARITH_DF64 = 2, SV_ARITH_TC = 3 } sv_arith;
 
 /* Run options; a null pointer or 0 fields mean "auto".
  *   max_fuse_k:   largest fused block, 1..5 qubits; 1 = no fusion (each gate
@@ -196,6 +206,7 @@ typedef struct {
     double  upload_bytes;    /* descriptors + coefficients copied host->device */
     double  alu_ops;         /* modelled ALU lane operations of the passes:
                                 FP32 ops (complex64, df64) or FP64 ops (native) */
+    double  tensor_flops;    /* SV_ARITH_TC: bfloat16 MMA flops of the digit products */
 } sv_apply_stats;
 int sv_last_stats(const sv_state* s, sv_apply_stats* out);
 

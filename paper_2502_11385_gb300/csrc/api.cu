@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -40,6 +42,9 @@ struct sv_state {
     size_t d_red_cap = 0;
     sv_apply_stats last{};
     bool failed = false;
+    // contents came from the caller (sv_set_amplitudes, sv_create_on): the
+    // tensor-core mode checks their magnitude once before relying on it
+    bool foreign = false;
     std::vector<cudaEvent_t> events;  // timing events, reused across calls
 };
 
@@ -106,11 +111,14 @@ int max_tile(int dt, const svk::DevInfo& di) {
 
 // complex128 defaults to double-float arithmetic (same 1e-12 parity as native
 // float64, about 3x faster on GB300's FP32 pipe); SV_ARITH_NATIVE forces FP64.
-int resolve_arith(int dt, const sv_run_opts* o) {
+// The tensor-core mode needs tiles of at least 8 qubits (an MMA n-tile spans
+// 8 groups of up to 5 qubits); smaller states use double-float arithmetic.
+int resolve_arith(int dt, const sv_run_opts* o, int n = 34) {
     if (dt == SV_C64) return SV_ARITH_NATIVE;
     int a = o ? o->arith : 0;
     if (a == SV_ARITH_NATIVE) return SV_ARITH_NATIVE;
-    return SV_ARITH_DF64;
+    if (a == SV_ARITH_DF64) return SV_ARITH_DF64;
+    return n >= 8 ? SV_ARITH_TC : SV_ARITH_DF64;  // SV_ARITH_TC and SV_ARITH_AUTO
 }
 
 svp::Plan plan_for(int n, int dt, const sv_gate* g, size_t ng, const sv_run_opts* o, int smem_max_m) {
@@ -124,22 +132,121 @@ svp::Plan plan_for(int n, int dt, const sv_gate* g, size_t ng, const sv_run_opts
     m = std::max(m, c + svp::kMaxFuse);
     svp::Machine mc;
     int ak = svp::AK_FP32;
-    if (dt == SV_C128) ak = resolve_arith(dt, o) == SV_ARITH_DF64 ? svp::AK_DF64 : svp::AK_FP64;
+    if (dt == SV_C128) {
+        const int a = resolve_arith(dt, o, n);
+        ak = a == SV_ARITH_DF64 ? svp::AK_DF64 : (a == SV_ARITH_TC ? svp::AK_TC : svp::AK_FP64);
+    }
     return svp::make_plan(n, g, ng, k, m, c, amp_bytes(dt), ak, mc);
 }
 
 // Serialises a plan into descriptors (passes by value, ops and coefficients
 // into one contiguous upload).
+struct Word16 {
+    uint32_t w[4];
+};
+
 struct Lowered {
     std::vector<DevPass> passes;
     std::vector<DevOp> ops;
-    std::vector<svp::cd> coef;
+    std::vector<svp::cd> coef;   // complex coefficients (FP32 / FP64 / df64 modes)
+    std::vector<Word16> tc;      // tensor-core mode: MMA fragments and Q62 phases
+    bool is_tc = false;
 };
 
-void lower(const svp::Plan& P, Lowered& L) {
+// ---- tensor-core lowering ------------------------------------------------
+int64_t q62_of(double x) {
+    const double v = std::ldexp(x, 62);
+    if (v >= 9.2233720368547758e18) return INT64_MAX;
+    if (v <= -9.2233720368547758e18) return -INT64_MAX;
+    return (int64_t)std::llround(v);
+}
+
+uint32_t bf16_of_digit(int d) {
+    float f = (float)d;
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u >> 16;  // exact: |d| <= 256
+}
+
+// Digit j of a Q62 value: 8-bit digits for blocks of up to 4 qubits (seven
+// digits), 7-bit digits for 5-qubit blocks (eight digits); the same split the
+// tensor-core kernel applies to the amplitudes.
+int tc_digit(int64_t q, int j, int db) {
+    const int top = 56 - db;
+    int64_t v = q >> 6;
+    if (db == 7) v >>= 1;
+    return j == 0 ? (int)(v >> top) : (int)((v >> (top - db * j)) & ((1 << db) - 1));
+}
+
+// Embeds a block of k < 3 qubits at tile positions pos[] into a 3-qubit block
+// (identity on the added positions); returns the new positions and matrix.
+void extend_to3(int k, const int* pos, const std::vector<svp::cd>& M, uint64_t local_pos_mask_avail, int* pos3,
+                std::vector<svp::cd>& M3) {
+    uint64_t used = 0;
+    for (int j = 0; j < k; j++) used |= 1ull << pos[j];
+    uint64_t all = used;
+    for (int p = 0; p < 64 && __builtin_popcountll(all) < 3; p++)
+        if (((local_pos_mask_avail >> p) & 1) && !((all >> p) & 1)) all |= 1ull << p;
+    int n3 = 0;
+    int src_bit[3] = {-1, -1, -1};  // matrix bit of the original block for new bit b, or -1
+    for (int p = 0; p < 64; p++)
+        if ((all >> p) & 1) {
+            for (int j = 0; j < k; j++)
+                if (pos[j] == p) src_bit[n3] = j;
+            pos3[n3++] = p;
+        }
+    const int D = 1 << k;
+    M3.assign(64, svp::cd(0, 0));
+    for (int r = 0; r < 8; r++)
+        for (int c = 0; c < 8; c++) {
+            bool same_extra = true;
+            int rr = 0, cc = 0;
+            for (int b = 0; b < 3; b++) {
+                const int rb = (r >> b) & 1, cb = (c >> b) & 1;
+                if (src_bit[b] < 0) same_extra = same_extra && rb == cb;
+                else {
+                    rr |= rb << src_bit[b];
+                    cc |= cb << src_bit[b];
+                }
+            }
+            if (same_extra) M3[r * 8 + c] = M[(size_t)rr * D + cc];
+        }
+}
+
+// Digit fragments of a complex D x D matrix in mma.m16n8k16 A-operand order.
+void tc_fragments(int k, const std::vector<svp::cd>& M, std::vector<Word16>& out) {
+    const int D = 1 << k, R = 2 * D, MT = R / 16, KT = R / 16;
+    std::vector<int64_t> q((size_t)R * R);
+    for (int r = 0; r < R; r++)
+        for (int c = 0; c < R; c++) {
+            const svp::cd u = M[(size_t)(r % D) * D + (c % D)];
+            double v;
+            if (r < D) v = c < D ? u.real() : -u.imag();
+            else v = c < D ? u.imag() : u.real();
+            q[(size_t)r * R + c] = q62_of(v);
+        }
+    const int db = 8, nd = 7;  // tensor-core blocks have at most 4 qubits
+    auto A = [&](int i, int row, int col) { return bf16_of_digit(tc_digit(q[(size_t)row * R + col], i, db)); };
+    for (int i = 0; i < nd; i++)
+        for (int mt = 0; mt < MT; mt++)
+            for (int ks = 0; ks < KT; ks++)
+                for (int lane = 0; lane < 32; lane++) {
+                    const int g = lane >> 2, t = lane & 3, r0 = mt * 16 + g, c0 = ks * 16 + 2 * t;
+                    Word16 w;
+                    w.w[0] = A(i, r0, c0) | (A(i, r0, c0 + 1) << 16);
+                    w.w[1] = A(i, r0 + 8, c0) | (A(i, r0 + 8, c0 + 1) << 16);
+                    w.w[2] = A(i, r0, c0 + 8) | (A(i, r0, c0 + 9) << 16);
+                    w.w[3] = A(i, r0 + 8, c0 + 8) | (A(i, r0 + 8, c0 + 9) << 16);
+                    out.push_back(w);
+                }
+}
+
+void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE) {
     L.passes.clear();
     L.ops.clear();
     L.coef.clear();
+    L.tc.clear();
+    L.is_tc = arith == SV_ARITH_TC;
     for (const auto& ps : P.passes) {
         DevPass dp;
         std::memset(&dp, 0, sizeof(dp));
@@ -171,9 +278,32 @@ void lower(const svp::Plan& P, Lowered& L) {
                 op.pos[j] = pos_of[b.qubits[j]];
                 op.qbit[j] = b.qubits[j];
             }
-            L.coef.insert(L.coef.end(), b.mat.begin(), b.mat.end());
+            if (L.is_tc) {
+                op.coeff = (int32_t)L.tc.size();
+                if (op.kind == svk::OP_DIAG) {
+                    for (const auto& u : b.mat) {
+                        const int64_t re = q62_of(u.real()), im = q62_of(u.imag());
+                        Word16 w;
+                        std::memcpy(&w.w[0], &re, 8);
+                        std::memcpy(&w.w[2], &im, 8);
+                        L.tc.push_back(w);
+                    }
+                } else if (b.k < 3) {
+                    int pos3[3];
+                    std::vector<svp::cd> M3;
+                    const uint64_t avail = ((1ull << ps.m) - 1);
+                    extend_to3(b.k, op.pos, b.mat, avail, pos3, M3);
+                    op.k = 3;
+                    for (int j = 0; j < 3; j++) op.pos[j] = pos3[j];
+                    tc_fragments(3, M3, L.tc);
+                } else {
+                    tc_fragments(b.k, b.mat, L.tc);
+                }
+            } else {
+                L.coef.insert(L.coef.end(), b.mat.begin(), b.mat.end());
+            }
             L.ops.push_back(op);
-            if (op.kind == svk::OP_DENSE) dp.kmax = std::max(dp.kmax, (int32_t)b.k);
+            if (op.kind == svk::OP_DENSE) dp.kmax = std::max(dp.kmax, (int32_t)op.k);
         }
         if (dp.kmax < 1) dp.kmax = 1;
         dp.n_ops = (int32_t)(L.ops.size() - dp.op0);
@@ -232,18 +362,26 @@ void write_coefs(const std::vector<svp::cd>& coef, int dt, int arith, unsigned c
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+size_t coef_bytes(const Lowered& L, int dt) {
+    return L.is_tc ? L.tc.size() * sizeof(Word16) : L.coef.size() * coef_elem_bytes(dt);
+}
+
 int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
     Lowered L;
-    lower(P, L);
+    lower(P, L, arith);
     const size_t ops_bytes = L.ops.size() * sizeof(DevOp);
     const size_t coef_off = align256(ops_bytes);
-    const size_t ent_off = align256(coef_off + L.coef.size() * coef_elem_bytes(s->dt));
+    const size_t ent_off = align256(coef_off + coef_bytes(L, s->dt));
     const size_t total = ent_off + L.passes.size() * sizeof(svk::BatchEntry);
     SV_TRY(ensure(&s->d_ws, &s->d_ws_cap, total, false));
     SV_TRY(ensure(&s->h_ws, &s->h_ws_cap, total, true));
     auto* h = (unsigned char*)s->h_ws;
     if (ops_bytes) std::memcpy(h, L.ops.data(), ops_bytes);
-    write_coefs(L.coef, s->dt, arith, h + coef_off);
+    if (L.is_tc) {
+        if (!L.tc.empty()) std::memcpy(h + coef_off, L.tc.data(), L.tc.size() * sizeof(Word16));
+    } else {
+        write_coefs(L.coef, s->dt, arith, h + coef_off);
+    }
     auto* ent = (svk::BatchEntry*)(h + ent_off);
     for (size_t i = 0; i < L.passes.size(); i++) {
         ent[i].state = (uint64_t)(uintptr_t)s->amp;
@@ -351,6 +489,7 @@ int sv_create_on(void* dev_ptr, size_t bytes, int n, int dt, void* stream, sv_st
     s->owned = false;
     s->stream = (cudaStream_t)stream;
     s->own_stream = false;
+    s->foreign = true;
     *out = s;
     return SV_OK;
 }
@@ -365,6 +504,7 @@ int sv_rebind(sv_state* s, void* dev_ptr, size_t bytes, int n, int dt) {
     s->dt = dt;
     s->bytes = bytes;
     s->failed = false;
+    s->foreign = true;
     s->last = sv_apply_stats{};
     return SV_OK;
 }
@@ -391,6 +531,7 @@ int sv_reset(sv_state* s, uint64_t basis) {
     SV_TRY(svk::launch_init(s->dt, s->amp, s->n, basis, s->stream, s->di));
     SV_TRY(cudaStreamSynchronize(s->stream));
     s->failed = false;
+    s->foreign = false;
     return SV_OK;
 }
 
@@ -404,7 +545,24 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     svp::Plan P = plan_for(s->n, s->dt, g, ng, o, max_tile(s->dt, s->di));
     if (o && o->debug_checks && svp::check_plan(P, ng, g) != 0) return SV_ERR_STATE;
     const double t1 = now_ms();
-    const int arith = resolve_arith(s->dt, o);
+    int arith = resolve_arith(s->dt, o, s->n);
+    if (arith == SV_ARITH_TC && s->foreign) {
+        // caller-supplied amplitudes: the fixed-point tile needs |re|, |im| <= 1
+        SV_TRY(ensure(&s->d_red, &s->d_red_cap, 256, false));
+        SV_TRY(svk::launch_max_abs_c128(s->amp, s->n, (unsigned long long*)s->d_red, s->stream, s->di));
+        unsigned long long bits = 0;
+        SV_TRY(cudaMemcpyAsync(&bits, s->d_red, 8, cudaMemcpyDeviceToHost, s->stream));
+        SV_TRY(cudaStreamSynchronize(s->stream));
+        double mx;
+        std::memcpy(&mx, &bits, 8);
+        if (mx <= 1.0) s->foreign = false;  // evolution by unitaries keeps it so
+        else arith = SV_ARITH_DF64;
+    }
+    if (arith != resolve_arith(s->dt, o, s->n)) {  // re-plan for double-float arithmetic
+        sv_run_opts df = o ? *o : sv_run_opts{};
+        df.arith = SV_ARITH_DF64;
+        P = plan_for(s->n, s->dt, g, ng, &df, max_tile(s->dt, s->di));
+    }
     rc = apply_plan(s, P, arith, o && o->timing);
     s->last.n_blocks = (int32_t)P.blocks.size();
     s->last.n_passes = (int32_t)P.passes.size();
@@ -413,6 +571,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     s->last.arith = arith;
     s->last.flops = P.flops;
     s->last.alu_ops = P.alu_ops;
+    s->last.tensor_flops = arith == SV_ARITH_TC ? P.mma_flops : 0.0;
     s->last.hbm_bytes = 2.0 * (double)s->bytes * (double)P.passes.size();
     s->last.plan_ms = t1 - t0;
     return rc;
@@ -480,6 +639,7 @@ int sv_set_amplitudes(sv_state* s, const void* in, size_t bytes, int in_is_devic
                            s->stream));
     SV_TRY(cudaStreamSynchronize(s->stream));
     s->failed = false;
+    s->foreign = true;
     return SV_OK;
 }
 
@@ -567,9 +727,9 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         bp.idx = (int)i;
         bp.n = it.n_qubits;
         bp.dt = it.dt;
-        bp.arith = resolve_arith(it.dt, opts);
+        bp.arith = resolve_arith(it.dt, opts, it.n_qubits);
         bp.plan = plan_for(it.n_qubits, it.dt, it.gates, it.n_gates, opts, max_tile(it.dt, b->di));
-        lower(bp.plan, bp.low);
+        lower(bp.plan, bp.low, bp.arith);
         bp.host_out = !it.probs_on_device;
         P.push_back(std::move(bp));
     }
@@ -586,7 +746,9 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         off += align256(((size_t)8) << bp.n);
     }
     // group by kernel mode (dtype, arithmetic)
-    auto mode_of = [](const BatchItemPlan& bp) { return bp.dt == SV_C64 ? 0 : (bp.arith == SV_ARITH_DF64 ? 2 : 1); };
+    auto mode_of = [](const BatchItemPlan& bp) {
+        return bp.dt == SV_C64 ? 0 : (bp.arith == SV_ARITH_DF64 ? 2 : (bp.arith == SV_ARITH_TC ? 3 : 1));
+    };
     std::vector<DevOp> ops;
     std::vector<unsigned char> coefs;  // per-mode coefficient blobs, concatenated
     struct Launch {
@@ -612,8 +774,12 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         // coefficient offsets are in elements; keep each item's blob aligned to its element size
         const size_t esz = coef_elem_bytes(bp.dt);
         size_t cb = (coefs.size() + esz - 1) / esz * esz;
-        coefs.resize(cb + bp.low.coef.size() * esz);
-        write_coefs(bp.low.coef, bp.dt, bp.arith, coefs.data() + cb);
+        coefs.resize(cb + coef_bytes(bp.low, bp.dt));
+        if (bp.low.is_tc) {
+            if (!bp.low.tc.empty()) std::memcpy(coefs.data() + cb, bp.low.tc.data(), bp.low.tc.size() * sizeof(Word16));
+        } else {
+            write_coefs(bp.low.coef, bp.dt, bp.arith, coefs.data() + cb);
+        }
         coef_base[i] = cb;
     }
     const size_t ops_off = off;
@@ -622,7 +788,7 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
     off += align256(coefs.size() + 16);
     // multi-state launches per (mode, pass index); the op/coef offsets inside each
     // entry's pass point at the item's ops; coefficient offsets are rebased below
-    for (int mode = 0; mode < 3; mode++) {
+    for (int mode = 0; mode < 4; mode++) {
         size_t max_passes = 0;
         std::vector<size_t> members;
         for (size_t i = 0; i < P.size(); i++)
@@ -689,7 +855,7 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
     for (auto& en : entries) en.state = (uint64_t)(uintptr_t)(A + P[(size_t)en.state].state_off);
     {
         size_t k = 0;
-        for (int mode = 0; mode < 3; mode++)
+        for (int mode = 0; mode < 4; mode++)
             for (size_t i = 0; i < P.size(); i++) {
                 if (mode_of(P[i]) != mode) continue;
                 sentries[k].state = (uint64_t)(uintptr_t)(A + P[i].state_off);

@@ -423,9 +423,235 @@ __device__ __forceinline__ void op_diag_df(DF4* sm, int m, const DevOp& op, cons
 }
 
 // ---------------------------------------------------------------------------
+// K5-tc: complex128 block products on the tensor cores (exact digit split).
+//
+// In this mode a tile holds every amplitude component as a Q62 fixed-point
+// int64 (x * 2^62; the components of a normalised state never exceed 1 in
+// magnitude).  A k-qubit block (k = 3 or 4; smaller blocks are padded with
+// identity qubits) y = U x is taken in real form (R = 2^(k+1) <= 32 rows and
+// columns: real parts, then imaginary parts) and both operands are split into
+// seven 8-bit digits, x = 2^6 sum_j X_j 2^(48 - 8j) (Q62 units; the top digit
+// is signed with |X_0| <= 256, the others are bytes), likewise the matrix,
+// whose digit fragments are prepared on the host.  Products of digits are
+// exact in bfloat16 x bfloat16 -> float32 MMAs and the partial sums of each
+// level L = i + j stay below 2^24 (at most 7 pairs x 32 terms x 2^16), so each
+// level is accumulated exactly in float32.  Levels 0..6 are kept (28 digit
+// pairs); y = sum_L Z_L 2^(46 - 8L) is re-assembled in int64 (the dropped
+// levels contribute below 2^-50 in magnitude).
+// ---------------------------------------------------------------------------
+struct alignas(16) Q2 {
+    long long re, im;
+};
+
+__device__ __forceinline__ long long d2q(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;
+    const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = e - 1013;  // x * 2^62 = m * 2^(e - 1013)
+    long long v;
+    if (sh > 10) v = 0x7FFFFFFFFFFFFFFFll;  // |x| >= 2: outside the fixed-point range (saturated)
+    else if (sh >= 0) v = (long long)(m << sh);
+    else if (sh > -64) v = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+    else v = 0;
+    return (b >> 63) ? -v : v;
+}
+
+__device__ __forceinline__ double q2d(long long q) {
+    if (q == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)q & 0x8000000000000000ull;
+    const unsigned long long a = sign ? (unsigned long long)(-q) : (unsigned long long)q;
+    const int lz = __clzll((long long)a);
+    const unsigned long long n = a << lz;  // leading one at bit 63
+    unsigned long long mant = n >> 11;
+    const unsigned long long rem = n & 0x7FFull;
+    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant++;  // round to nearest even
+    unsigned long long E = (unsigned long long)(1023 + 1 - lz);      // value = a * 2^-62
+    if (mant >> 53) {
+        mant >>= 1;
+        E++;
+    }
+    return __longlong_as_double((long long)(sign | (E << 52) | (mant & ((1ull << 52) - 1))));
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint4& a, unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b0), "r"(b1));
+}
+
+// bfloat16 bits of byte k (0..3) of word w, as an exact integer in [0, 255]:
+// 2^23 + b is assembled with one byte permute, then 2^23 is subtracted.
+__device__ __forceinline__ unsigned bf16_byte_pair(unsigned w0, unsigned w1, unsigned sel) {
+    const unsigned f0 = __byte_perm(w0, 0x4B000000u, sel);
+    const unsigned f1 = __byte_perm(w1, 0x4B000000u, sel);
+    const float g0 = __uint_as_float(f0) - 8388608.0f;
+    const float g1 = __uint_as_float(f1) - 8388608.0f;
+    return __byte_perm(__float_as_uint(g0), __float_as_uint(g1), 0x7632);  // high halves: bf16(g0) | bf16(g1) << 16
+}
+
+// Signed top digit d0 = v >> 48 of two values (|d0| <= 256), packed as bf16 x 2.
+__device__ __forceinline__ unsigned bf16_top_pair(long long v0, long long v1) {
+    const int d0 = (int)(v0 >> 48), d1 = (int)(v1 >> 48);
+    const float g0 = __int_as_float(0x4B400000 + d0) - 12582912.0f;
+    const float g1 = __int_as_float(0x4B400000 + d1) - 12582912.0f;
+    return __byte_perm(__float_as_uint(g0), __float_as_uint(g1), 0x7632);
+}
+
+// Seven 8-bit digits of two Q62 values x0, x1 (v = x >> 6; digit 0 = v >> 48
+// signed, digit j >= 1 = byte 6 - j of v), packed pairwise as bf16 x 2.
+__device__ __forceinline__ void tc_digits_pair(long long x0, long long x1, unsigned (&out)[7]) {
+    const long long v0 = x0 >> 6, v1 = x1 >> 6;
+    const unsigned lo0 = (unsigned)v0, hi0 = (unsigned)((unsigned long long)v0 >> 32);
+    const unsigned lo1 = (unsigned)v1, hi1 = (unsigned)((unsigned long long)v1 >> 32);
+    out[0] = bf16_top_pair(v0, v1);
+    out[1] = bf16_byte_pair(hi0, hi1, 0x7541);  // byte 5 of v = byte 1 of hi
+    out[2] = bf16_byte_pair(hi0, hi1, 0x7540);  // byte 4 = byte 0 of hi
+    out[3] = bf16_byte_pair(lo0, lo1, 0x7543);
+    out[4] = bf16_byte_pair(lo0, lo1, 0x7542);
+    out[5] = bf16_byte_pair(lo0, lo1, 0x7541);
+    out[6] = bf16_byte_pair(lo0, lo1, 0x7540);
+}
+
+// Dense block of 3 or 4 qubits on the tensor cores (8-bit digits, levels 0..6).
+// A fragments: Af[((i * MT + mt) * KT + ks) * 32 + lane] for digit i, m-tile mt,
+// k-step ks.  Each warp takes n-tiles of 8 groups.  Real-form row / column k
+// of a block is the real part of amplitude k (k < D) or the imaginary part of
+// amplitude k - D.
+template <int K>
+__device__ __forceinline__ void op_dense_tc(Q2* sm, int m, const DevOp& op, const uint4* __restrict__ Af) {
+    static_assert(K == 3 || K == 4, "tensor-core blocks have 3 or 4 qubits");
+    constexpr int D = 1 << K, R = 2 * D, MT = R / 16, KT = R / 16;
+    constexpr int ND = 7, NL = 7;
+    int pos[K], pm[K];
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        pos[j] = op.pos[j];
+        pm[j] = 1 << pos[j];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int ng = 1 << (m - K), ntiles = ng >> 3;
+    for (int nt = warp; nt < ntiles; nt += nwarps) {
+        // B operand: this lane's column is group g of the n-tile; its rows in
+        // k-step ks are ks*16 + {2t, 2t+1, 2t+8, 2t+9}.  Each amplitude it needs
+        // is loaded once and both its real and imaginary digits are formed.
+        const int bg = swz<double>(insert_zero_bits<K>(nt * 8 + g, pos));
+        unsigned bf[KT][ND][2];
+        if constexpr (K == 3) {
+            // one k-step: rows 2t, 2t+1 = re of amplitudes 2t, 2t+1; rows 2t+8, 2t+9 = their im
+            const Q2 a0 = sm[bg ^ swz<double>(group_offset<K>(2 * t, pm))];
+            const Q2 a1 = sm[bg ^ swz<double>(group_offset<K>(2 * t + 1, pm))];
+            unsigned dre[ND], dim_[ND];
+            tc_digits_pair(a0.re, a1.re, dre);
+            tc_digits_pair(a0.im, a1.im, dim_);
+#pragma unroll
+            for (int j = 0; j < ND; j++) {
+                bf[0][j][0] = dre[j];
+                bf[0][j][1] = dim_[j];
+            }
+        } else {
+            // k-step 0: re of amplitudes {2t, 2t+1, 2t+8, 2t+9}; k-step 1: their im
+            const Q2 a0 = sm[bg ^ swz<double>(group_offset<K>(2 * t, pm))];
+            const Q2 a1 = sm[bg ^ swz<double>(group_offset<K>(2 * t + 1, pm))];
+            const Q2 a2 = sm[bg ^ swz<double>(group_offset<K>(2 * t + 8, pm))];
+            const Q2 a3 = sm[bg ^ swz<double>(group_offset<K>(2 * t + 9, pm))];
+            unsigned d[ND];
+            tc_digits_pair(a0.re, a1.re, d);
+#pragma unroll
+            for (int j = 0; j < ND; j++) bf[0][j][0] = d[j];
+            tc_digits_pair(a2.re, a3.re, d);
+#pragma unroll
+            for (int j = 0; j < ND; j++) bf[0][j][1] = d[j];
+            tc_digits_pair(a0.im, a1.im, d);
+#pragma unroll
+            for (int j = 0; j < ND; j++) bf[1][j][0] = d[j];
+            tc_digits_pair(a2.im, a3.im, d);
+#pragma unroll
+            for (int j = 0; j < ND; j++) bf[1][j][1] = d[j];
+        }
+        // Every lane has built its B fragments before the first mma.sync (the
+        // instruction is warp-wide), so each m-tile's outputs can be written as
+        // soon as they are assembled.
+        // A fragments are fetched one digit ahead so each load overlaps the
+        // MMAs of the previous digit
+        uint4 a_next = Af[lane];  // digit 0, m-tile 0, k-step 0
+#pragma unroll 1
+        for (int mt = 0; mt < MT; mt++) {
+            float acc[NL][4];
+#pragma unroll
+            for (int L = 0; L < NL; L++) acc[L][0] = acc[L][1] = acc[L][2] = acc[L][3] = 0.f;
+#pragma unroll
+            for (int ks = 0; ks < KT; ks++) {
+#pragma unroll
+                for (int i = 0; i < ND; i++) {
+                    const uint4 a = a_next;
+                    // next (digit, k-step) of this m-tile, else digit 0 of the next m-tile
+                    const int ni = i + 1 < ND ? i + 1 : 0;
+                    const int nks = i + 1 < ND ? ks : ks + 1;
+                    const int nmt = (i + 1 < ND || ks + 1 < KT) ? mt : mt + 1;
+                    if (nmt < MT) a_next = Af[((ni * MT + nmt) * KT + (nks < KT ? nks : 0)) * 32 + lane];
+#pragma unroll
+                    for (int j = 0; j < ND; j++)
+                        if (i + j < NL) mma_bf16_16816(acc[i + j], a, bf[ks][j][0], bf[ks][j][1]);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                // y = sum_L Z_L 2^(46 - 8L) in Q62 units (Horner over L = 0..5,
+                // level 6 carries weight 2^-2); two's-complement wrap is harmless
+                unsigned long long v = (unsigned long long)(long long)__float2int_rn(acc[0][e]);
+#pragma unroll
+                for (int L = 1; L < NL - 1; L++)
+                    v = (v << 8) + (unsigned long long)(long long)__float2int_rn(acc[L][e]);
+                v = (v << 6) + (unsigned long long)(long long)((__float2int_rn(acc[NL - 1][e]) + 2) >> 2);
+                const int row = mt * 16 + g + ((e >> 1) << 3);
+                const int col = 2 * t + (e & 1);
+                const int b = row & (D - 1);
+                const int cg = swz<double>(insert_zero_bits<K>(nt * 8 + col, pos));
+                Q2* dst = &sm[cg ^ swz<double>(group_offset<K>(b, pm))];
+                if (row >> K) dst->im = (long long)v;
+                else dst->re = (long long)v;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// Q62 x Q62 -> Q62 (floor)
+__device__ __forceinline__ long long qmul(long long a, long long b) {
+    const long long hi = __mul64hi(a, b);
+    const unsigned long long lo = (unsigned long long)(a * b);
+    return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
+}
+
+__device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const Q2* __restrict__ M,
+                                           uint64_t tile_base) {
+    const DiagIndex d = diag_index<double>(op, tile_base);
+    const int N = 1 << m;
+    const int iters = (N + 255) >> 8;
+    const bool sign_only = op.flags & OPF_SIGN_ONLY;
+    for (int it = 0; it < iters; it++) {
+        if ((int)threadIdx.x + (it << 8) >= N) break;
+        int idx, si;
+        diag_at<double>(d, it, idx, si);
+        const Q2 u = M[idx];
+        const Q2 a = sm[si];
+        if (sign_only) {
+            if (u.re < 0) sm[si] = Q2{-a.re, -a.im};
+        } else {
+            sm[si] = Q2{qmul(u.re, a.re) - qmul(u.im, a.im), qmul(u.re, a.im) + qmul(u.im, a.re)};
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // K5: the tile-pass kernel, shared by the three arithmetic modes.
 // ---------------------------------------------------------------------------
-enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2 };
+enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2, MODE_TC = 3 };
 
 template <int MODE>
 struct TileTraits;
@@ -450,11 +676,26 @@ struct TileTraits<MODE_DF> {
     using Coef = DF4;
     using SwzT = double;
 };
+template <>
+struct TileTraits<MODE_TC> {
+    using Store = Cx<double>;
+    using Smem = Q2;
+    using Coef = uint4;  // dense: MMA fragments; diagonal: Q2 entries
+    using SwzT = double;
+};
 
 template <int MODE, int KMAX>
 __device__ __forceinline__ void apply_op(typename TileTraits<MODE>::Smem* sm, int m, const DevOp& op,
                                          const typename TileTraits<MODE>::Coef* __restrict__ M, uint64_t base) {
-    if constexpr (MODE == MODE_DF) {
+    if constexpr (MODE == MODE_TC) {
+        if (op.kind == OP_DIAG) {
+            op_diag_tc(sm, m, op, reinterpret_cast<const Q2*>(M), base);
+        } else if (op.k <= 3) {
+            op_dense_tc<3>(sm, m, op, M);
+        } else {
+            op_dense_tc<(KMAX >= 4 ? 4 : 3)>(sm, m, op, M);  // the planner caps these blocks at 4 qubits
+        }
+    } else if constexpr (MODE == MODE_DF) {
         if (op.kind == OP_DIAG) {
             op_diag_df(sm, m, op, M, base);
         } else if (op.k == 1) {
@@ -491,7 +732,7 @@ __device__ __forceinline__ void apply_op(typename TileTraits<MODE>::Smem* sm, in
 // apply the pass's ops in order, scatter the tile back.  Persistent: each CTA
 // strides over the flattened tile space of all entries.
 template <int MODE, int KMAX>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, MODE == MODE_TC ? 2 : 1)
     k_tile_pass(const BatchEntry* __restrict__ E, int n_entries, uint64_t total_tiles, const DevOp* __restrict__ ops,
                 const typename TileTraits<MODE>::Coef* __restrict__ coef) {
     using Tr = TileTraits<MODE>;
@@ -551,6 +792,14 @@ __global__ void __launch_bounds__(kTileThreads)
                 d2df(a.im, v.ih, v.il);
                 sm[swz<double>(j)] = v;
             }
+        } else if constexpr (MODE == MODE_TC) {
+            const int N = 1 << m;
+            for (int j = threadIdx.x; j < N; j += blockDim.x) {
+                const int r = j >> c;
+                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                const Cx<double> a = st[gidx];
+                sm[swz<double>(j)] = Q2{d2q(a.re), d2q(a.im)};
+            }
         } else {
             constexpr int PER = 16 / sizeof(Store);  // amplitudes per 16-byte vector
             const int nvec = (1 << m) / PER;
@@ -575,6 +824,14 @@ __global__ void __launch_bounds__(kTileThreads)
                 const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
                 const DF4 v = sm[swz<double>(j)];
                 st[gidx] = Cx<double>{df2d(v.rh, v.rl), df2d(v.ih, v.il)};
+            }
+        } else if constexpr (MODE == MODE_TC) {
+            const int N = 1 << m;
+            for (int j = threadIdx.x; j < N; j += blockDim.x) {
+                const int r = j >> c;
+                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                const Q2 v = sm[swz<double>(j)];
+                st[gidx] = Cx<double>{q2d(v.re), q2d(v.im)};
             }
         } else {
             constexpr int PER = 16 / sizeof(Store);
@@ -722,6 +979,23 @@ __global__ void k_bins_to_double(const unsigned long long* __restrict__ bins, ui
         out[b] = fixed_to_double(((unsigned __int128)bins[2 * b + 1] << 64) | bins[2 * b]);
 }
 
+// Largest |component| of a state, as the bit pattern of a non-negative
+// double (such patterns order like the values): atomicMax into *out.
+__global__ void k_max_abs(const double* __restrict__ a, uint64_t n, unsigned long long* out) {
+    unsigned long long m = 0;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(a[i]) & 0x7FFFFFFFFFFFFFFFull;
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long x = __shfl_down_sync(0xffffffffu, m, o);
+        m = x > m ? x : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
 __global__ void k_zero_u64(unsigned long long* p, uint64_t n) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) p[i] = 0ull;
@@ -819,6 +1093,8 @@ cudaError_t launch_tile_pass(int dt, int arith, const BatchEntry* d_entries, int
         return tile_pass_mode<MODE_F32>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
     if (arith == SV_ARITH_DF64)
         return tile_pass_mode<MODE_DF>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+    if (arith == SV_ARITH_TC)
+        return tile_pass_mode<MODE_TC>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
     return tile_pass_mode<MODE_F64>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
 }
 
@@ -837,6 +1113,14 @@ cudaError_t launch_probs_multi(int dt, const StateEntry* d_entries, int n_entrie
     const unsigned grid = grid_for(total_amps, 256, di, 8);
     if (dt == SV_C64) k_probs_multi<float><<<grid, 256, 0, s>>>(d_entries, n_entries);
     else k_probs_multi<double><<<grid, 256, 0, s>>>(d_entries, n_entries);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_max_abs_c128(const void* amp, int n, unsigned long long* d_out, cudaStream_t s,
+                               const DevInfo& di) {
+    const uint64_t count = 2ull << n;  // re and im of 2^n amplitudes
+    k_zero_u64<<<1, 32, 0, s>>>(d_out, 1);
+    k_max_abs<<<grid_for(count, 256, di), 256, 0, s>>>((const double*)amp, count, d_out);
     return cudaGetLastError();
 }
 

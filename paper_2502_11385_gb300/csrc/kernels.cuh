@@ -37,6 +37,10 @@ cudaError_t launch_init_multi(int dt, const StateEntry* d_entries, int n_entries
 cudaError_t launch_probs_multi(int dt, const StateEntry* d_entries, int n_entries, uint64_t total_amps,
                                cudaStream_t s, const DevInfo& di);
 
+// *d_out = bit pattern of max |re|, |im| over a complex128 state.
+cudaError_t launch_max_abs_c128(const void* amp, int n, unsigned long long* d_out, cudaStream_t s,
+                               const DevInfo& di);
+
 // p[i - i0] = |amp_i|^2 for i in [i0, i0 + len) (K7, probability part).
 cudaError_t launch_probs(int dt, const void* amp, uint64_t i0, uint64_t len, double* p,
                          cudaStream_t s, const DevInfo& di);

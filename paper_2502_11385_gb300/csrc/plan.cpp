@@ -237,28 +237,46 @@ static double block_instr(const Block& b, int arith) {
     return (arith == AK_DF64 ? 44.0 : 4.0) * D;
 }
 
-double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops, double* alu_ops) {
+// Tensor-core mode: bfloat16 MMA flops per amplitude of a dense block (43
+// digit pairs of a real 2D x 2D product, blocks of fewer than 3 qubits padded
+// to 3) and CUDA-core operations per amplitude (digit split, re-assembly).
+static double tc_mma_flops(const Block& b) {
+    if (b.kind == BK_DIAG) return 0.0;
+    const int k = std::max(3, b.k);
+    return 28.0 * 8.0 * (double)(1 << k);  // 28 digit pairs of a real 2^(k+1) square product
+}
+static double tc_alu(const Block& b) { return b.kind == BK_DIAG ? (b.sign_only ? 2.0 : 40.0) : 150.0; }
+
+double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops, double* alu_ops,
+                  double* mma_flops) {
     const double dim = std::ldexp(1.0, p.n);
     const double state = dim * amp_bytes;
     const double rate = arith == AK_FP64 ? mc.fp64_ips : mc.fp32_ips;
-    double total = 0, fl_all = 0, ops_all = 0;
+    double total = 0, fl_all = 0, ops_all = 0, mma_all = 0;
     for (const auto& ps : p.passes) {
-        double fl = 0, instr = 0, smem = 0;
+        double fl = 0, instr = 0, smem = 0, mma = 0;
         for (int bi : ps.blocks) {
             fl += block_flops(p.blocks[bi], dim);
-            instr += block_instr(p.blocks[bi], arith) * dim;
+            if (arith == AK_TC) {
+                instr += tc_alu(p.blocks[bi]) * dim;
+                mma += tc_mma_flops(p.blocks[bi]) * dim;
+            } else {
+                instr += block_instr(p.blocks[bi], arith) * dim;
+            }
             smem += 2.0 * state;
         }
-        if (arith == AK_DF64) instr += 60.0 * dim;  // float64 <-> double-float conversions per pass
+        if (arith == AK_DF64 || arith == AK_TC) instr += 60.0 * dim;  // float64 conversions per pass
         fl_all += fl;
         ops_all += instr;
-        const double alu = instr / rate;
+        mma_all += mma;
+        const double alu = instr / rate + mma / mc.mma_flops;
         const double hbm = 2.0 * state / mc.hbm_Bps;
         const double sm = smem / mc.smem_Bps;
         total += std::max(std::max(alu, hbm), sm) + mc.launch_s;
     }
     if (flops) *flops = fl_all;
     if (alu_ops) *alu_ops = ops_all;
+    if (mma_flops) *mma_flops = mma_all;
     return total;
 }
 
@@ -267,6 +285,10 @@ Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int c
     Plan best;
     best.model_s = 1e300;
     int k_lo = fuse_k > 0 ? fuse_k : 1, k_hi = fuse_k > 0 ? fuse_k : kMaxFuse;
+    if (arith == AK_TC) {  // tensor-core blocks have at most 4 qubits
+        k_hi = std::min(k_hi, 4);
+        k_lo = std::min(k_lo, k_hi);
+    }
     for (int k = k_lo; k <= k_hi; k++) {
         Plan p;
         p.n = n;
@@ -289,10 +311,11 @@ Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int c
         if (p.model_s < best.model_s) best = std::move(p);
     }
     finalize(best.blocks, g);
-    double fl = 0, ops = 0;
-    best.model_s = model_cost(best, amp_bytes, arith, mc, &fl, &ops);
+    double fl = 0, ops = 0, mma = 0;
+    best.model_s = model_cost(best, amp_bytes, arith, mc, &fl, &ops, &mma);
     best.flops = fl;
     best.alu_ops = ops;
+    best.mma_flops = mma;
     return best;
 }
 

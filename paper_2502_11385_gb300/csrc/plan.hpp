@@ -55,18 +55,20 @@ struct Plan {
     std::vector<Pass> passes;
     double flops = 0;      // modelled real flops (FMA = 2)
     double alu_ops = 0;    // modelled ALU lane operations (FP32 for df64/complex64, FP64 native)
+    double mma_flops = 0;  // tensor-core mode: bfloat16 MMA flops of the digit products
     double model_s = 0;    // modelled time
 };
 
 // Arithmetic of the tile kernels: float32 (complex64), native float64, or
 // double-float pairs on the FP32 units (complex128).
-enum ArithKind { AK_FP32 = 0, AK_FP64 = 1, AK_DF64 = 2 };
+enum ArithKind { AK_FP32 = 0, AK_FP64 = 1, AK_DF64 = 2, AK_TC = 3 };
 
 struct Machine {           // throughput model used by the autotuner (measured on GB300)
     double hbm_Bps = 6.6e12;
     double fp32_ips = 3.2e13;   // FP32 lane instructions per second (FFMA / FADD / FMUL)
     double fp64_ips = 4.6e11;   // FP64 lane instructions per second
     double smem_Bps = 3.5e13;
+    double mma_flops = 5.8e14;  // bfloat16 mma.sync, dense
     double launch_s = 4e-6;
 };
 
@@ -85,7 +87,7 @@ std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, 
 // Modelled cost of a plan (seconds) for a state of `amp_bytes` per amplitude;
 // *flops receives the real flops of the block products (FMA = 2).
 double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops,
-                  double* alu_ops = nullptr);
+                  double* alu_ops = nullptr, double* mma_flops = nullptr);
 
 // Full planning with optional autotuning over fuse_k (0 = auto).
 Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int coalesce,

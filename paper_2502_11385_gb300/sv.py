@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libsv.so")
 SV_OK, SV_ERR_ARG, SV_ERR_QUBIT, SV_ERR_OOM, SV_ERR_SIZE, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 C64, C128 = 0, 1
-ARITH_AUTO, ARITH_NATIVE, ARITH_DF64 = 0, 1, 2
+ARITH_AUTO, ARITH_NATIVE, ARITH_DF64, ARITH_TC = 0, 1, 2, 3
 DTYPES = {"c64": C64, "c128": C128, C64: C64, C128: C128}
 NP_DTYPE = {C64: np.complex64, C128: np.complex128}
 
@@ -42,7 +42,8 @@ class ApplyStats(ctypes.Structure):
                 ("tile_qubits", ctypes.c_int32), ("arith", ctypes.c_int32), ("n_launches", ctypes.c_int32),
                 ("flops", ctypes.c_double), ("hbm_bytes", ctypes.c_double), ("plan_ms", ctypes.c_double),
                 ("kernel_ms", ctypes.c_double), ("max_kernel_ms", ctypes.c_double),
-                ("upload_bytes", ctypes.c_double), ("alu_ops", ctypes.c_double)]
+                ("upload_bytes", ctypes.c_double), ("alu_ops", ctypes.c_double),
+                ("tensor_flops", ctypes.c_double)]
 
 
 class BatchItem(ctypes.Structure):

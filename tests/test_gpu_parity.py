@@ -295,7 +295,7 @@ def test_batch_matches_solo_bitwise_and_oracle(sv):
     for i, (n, dt) in enumerate(specs):
         g = _random_circuit(n, 60 + 5 * i, 400 + i)
         items.append((n, dt, g, None))
-    for arith in (sv.ARITH_NATIVE, sv.ARITH_DF64):
+    for arith in (sv.ARITH_NATIVE, sv.ARITH_DF64, sv.ARITH_TC):
         opts = sv.run_opts(arith=arith)
         with sv.Batch(items, opts) as b:
             assert b.status == [0] * len(items)
@@ -381,3 +381,62 @@ def test_cut_variants_shared_work_matches_plain(sv, dtype):
         from oracle import cut
         rec = cut.reconstruct(up, down, cc.width_a, list(cc.cut_qubits))
         assert np.abs(rec - oracle.probabilities(oracle.run(13, cc.full))).max() <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# complex128 on the tensor cores (SV_ARITH_TC: exact digit split)
+# ---------------------------------------------------------------------------
+def test_tc_brickwork12(sv):
+    g = W.workload_brickwork12()
+    ref = oracle.run(12, g)
+    for k in (1, 3, 4, 5):
+        st = _check(sv, 12, "c128", g, ref, max_fuse_k=k, arith=sv.ARITH_TC)
+        assert st["arith"] == sv.ARITH_TC
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n,tile", [(9, 0), (16, 9), (20, 0)])
+def test_tc_random_circuits(sv, n, tile, k):
+    g = _random_circuit(n, 120, 9000 * n + k)
+    _check(sv, n, "c128", g, max_fuse_k=k, tile_qubits=tile, arith=sv.ARITH_TC)
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_tc_every_gate_on_every_operand(sv, n):
+    prep = _random_circuit(n, 3 * n, 27 + n, ops=[W.U3, W.CX])
+    rows = []
+    for op in range(14):
+        for q0 in range(n):
+            if op >= W.CX:
+                rows += [(op, q0, q1, 0.37 + q0 - 0.11 * q1) for q1 in range(n) if q1 != q0]
+            else:
+                rows.append((op, q0, -1, 0.3 + 0.7 * q0, -1.1 + q0, 2.3 - q0))
+    g = W.concat(prep, W.gates(rows))
+    ref = oracle.run(n, g)
+    for k in (1, 3, 4, 5):
+        _check(sv, n, "c128", g, ref, max_fuse_k=k, arith=sv.ARITH_TC)
+
+
+def test_tc_small_states_fall_back(sv):
+    g = _random_circuit(5, 40, 5)
+    st = _check(sv, 5, "c128", g, arith=sv.ARITH_TC)
+    assert st["arith"] == sv.ARITH_DF64
+
+
+def test_auto_arith_falls_back_for_unnormalised_amplitudes(sv):
+    """A caller-supplied state with components above 1 in magnitude is outside
+    the tensor-core mode's fixed-point range: the call uses double-float."""
+    n = 10
+    rng = np.random.default_rng(4)
+    v = 3.0 * (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n))
+    g = _random_circuit(n, 30, 77)
+    with sv.State(n, "c128") as s:
+        s.set_amplitudes(v)
+        s.apply_circuit(g)
+        assert s.stats()["arith"] == sv.ARITH_DF64
+        ref = oracle.apply(n, v.astype(np.complex128).copy(), g)
+        assert np.abs(s.amplitudes() - ref).max() <= 1e-11
+        s.set_amplitudes(v / np.linalg.norm(v))
+        s.apply_circuit(g)
+        assert s.stats()["arith"] == sv.ARITH_TC
+        assert np.abs(s.amplitudes() - oracle.apply(n, (v / np.linalg.norm(v)).copy(), g)).max() <= 1e-12
