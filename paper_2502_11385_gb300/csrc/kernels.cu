@@ -601,13 +601,17 @@ __device__ __forceinline__ void op_dense_tc(Q2* sm, int m, const DevOp& op, cons
             __syncwarp();
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                // y = sum_L Z_L 2^(46 - 8L) in Q62 units (Horner over L = 0..5,
-                // level 6 carries weight 2^-2); two's-complement wrap is harmless
-                unsigned long long v = (unsigned long long)(long long)__float2int_rn(acc[0][e]);
+                // y = sum_L Z_L 2^(46 - 8L) in Q62 units = 2^6 (P01 2^32 + P23 2^16 +
+                // P45) + Z_6 / 4 with P_ab = 256 Z_a + Z_b formed as 64-bit products
+                // (|Z_L| <= (L+1) 2^21); two's-complement wrap of the sums is harmless
+                long long z[NL];
 #pragma unroll
-                for (int L = 1; L < NL - 1; L++)
-                    v = (v << 8) + (unsigned long long)(long long)__float2int_rn(acc[L][e]);
-                v = (v << 6) + (unsigned long long)(long long)((__float2int_rn(acc[NL - 1][e]) + 2) >> 2);
+                for (int L = 0; L < NL; L++) z[L] = __float2int_rn(acc[L][e]);
+                const unsigned long long p01 = (unsigned long long)(z[0] * 256 + z[1]);
+                const unsigned long long p23 = (unsigned long long)(z[2] * 256 + z[3]);
+                const unsigned long long p45 = (unsigned long long)(z[4] * 256 + z[5]);
+                unsigned long long v = (p01 << 32) + (p23 << 16) + p45;
+                v = (v << 6) + (unsigned long long)((z[6] + 2) >> 2);
                 const int row = mt * 16 + g + ((e >> 1) << 3);
                 const int col = 2 * t + (e & 1);
                 const int b = row & (D - 1);
