@@ -73,19 +73,33 @@ typedef struct {
  *                    Dekker 1971; Joldes, Muller, Popescu 2017), about 47
  *                    significant bits per operation.
  *   SV_ARITH_TC:     float64 storage, the state held in Q62 fixed point in
- *                    shared memory, block products on the tensor cores with
- *                    an exact split into 7-bit digits (bfloat16 products,
- *                    exact float32 level sums; error below 2^-51 per
- *                    product); requires amplitude components of magnitude
- *                    at most 1 (any normalised state).
+ *                    shared memory, fused-block products on the tensor cores
+ *                    (tcgen05.mma, accumulators in tensor memory) with an
+ *                    exact split of both operands into seven balanced 8-bit
+ *                    digits: bfloat16 digit products, exact float32 sums per
+ *                    digit level, levels 0..6 re-assembled in int64 (error
+ *                    about 1e-16 per block product, see the tile-pass notes
+ *                    in the kernels); requires amplitude components of
+ *                    magnitude at most 1 (any normalised state).
+ *   SV_ARITH_TC_SYNC: the same digit products on the warp-level mma.sync
+ *                    path (unsigned lower digits), kept as the measured
+ *                    baseline of the tensor-memory kernel.
  *   SV_ARITH_AUTO:   SV_ARITH_TC for states of 8 or more qubits, else
  *                    SV_ARITH_DF64 (on GB300 the FP64 pipe runs at about 1/70
  *                    of the FP32 pipe).  Amplitudes supplied by the caller
  *                    (sv_set_amplitudes, sv_create_on) are checked once:
  *                    if a component exceeds 1 in magnitude the call uses
- *                    SV_ARITH_DF64 instead.
+ *                    SV_ARITH_DF64 instead; so does a block whose digit sums
+ *                    could exceed the exact float32 range (none for unitary
+ *                    blocks).
  * complex64 states always compute in float32. */
-typedef enum { SV_ARITH_AUTO = 0, SV_ARITH_NATIVE = 1, SV_ARITH_DF64 = 2, SV_ARITH_TC = 3 } sv_arith;
+typedef enum {
+    SV_ARITH_AUTO = 0,
+    SV_ARITH_NATIVE = 1,
+    SV_ARITH_DF64 = 2,
+    SV_ARITH_TC = 3,
+    SV_ARITH_TC_SYNC = 4
+} sv_arith;
 
 /* Run options; a null pointer or 0 fields mean "auto".
  *   max_fuse_k:   largest fused block, 1..5 qubits; 1 = no fusion (each gate

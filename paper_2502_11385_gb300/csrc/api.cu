@@ -100,8 +100,12 @@ cudaError_t device_info(svk::DevInfo* out) {
 }
 
 // Tile shape per dtype: 2^m amplitudes in shared memory, the lowest c qubits
-// always in the tile (runs of 2^c contiguous amplitudes = 256 bytes).
-int default_tile(int dt) { return dt == SV_C64 ? 13 : 12; }
+// always in the tile (runs of 2^c contiguous amplitudes = 256 bytes).  The
+// tensor-memory mode takes 128 KiB tiles (one CTA per SM, 16 warps).
+int default_tile(int dt, int arith = SV_ARITH_NATIVE) {
+    if (dt == SV_C64) return 13;
+    return arith == SV_ARITH_TC ? 13 : 12;
+}
 int coalesce_of(int dt) { return dt == SV_C64 ? 5 : 4; }
 int max_tile(int dt, const svk::DevInfo& di) {
     int m = dt == SV_C64 ? 14 : 13;
@@ -118,24 +122,25 @@ int resolve_arith(int dt, const sv_run_opts* o, int n = 34) {
     int a = o ? o->arith : 0;
     if (a == SV_ARITH_NATIVE) return SV_ARITH_NATIVE;
     if (a == SV_ARITH_DF64) return SV_ARITH_DF64;
-    return n >= 8 ? SV_ARITH_TC : SV_ARITH_DF64;  // SV_ARITH_TC and SV_ARITH_AUTO
+    if (n < 8) return SV_ARITH_DF64;
+    return a == SV_ARITH_TC_SYNC ? SV_ARITH_TC_SYNC : SV_ARITH_TC;  // SV_ARITH_TC and SV_ARITH_AUTO
 }
+
+bool is_tc(int arith) { return arith == SV_ARITH_TC || arith == SV_ARITH_TC_SYNC; }
 
 svp::Plan plan_for(int n, int dt, const sv_gate* g, size_t ng, const sv_run_opts* o, int smem_max_m) {
     int k = o ? o->max_fuse_k : 0;
     if (k < 0) k = 0;
     if (k > svp::kMaxFuse) k = svp::kMaxFuse;
     const int c = coalesce_of(dt);
-    int m = (o && o->tile_qubits > 0) ? o->tile_qubits : default_tile(dt);
+    const int arith = dt == SV_C128 ? resolve_arith(dt, o, n) : SV_ARITH_NATIVE;
+    int m = (o && o->tile_qubits > 0) ? o->tile_qubits : default_tile(dt, arith);
     m = std::min(m, smem_max_m);
     m = std::min(m, c + 10);
     m = std::max(m, c + svp::kMaxFuse);
     svp::Machine mc;
     int ak = svp::AK_FP32;
-    if (dt == SV_C128) {
-        const int a = resolve_arith(dt, o, n);
-        ak = a == SV_ARITH_DF64 ? svp::AK_DF64 : (a == SV_ARITH_TC ? svp::AK_TC : svp::AK_FP64);
-    }
+    if (dt == SV_C128) ak = arith == SV_ARITH_DF64 ? svp::AK_DF64 : (is_tc(arith) ? svp::AK_TC : svp::AK_FP64);
     return svp::make_plan(n, g, ng, k, m, c, amp_bytes(dt), ak, mc);
 }
 
@@ -149,8 +154,9 @@ struct Lowered {
     std::vector<DevPass> passes;
     std::vector<DevOp> ops;
     std::vector<svp::cd> coef;   // complex coefficients (FP32 / FP64 / df64 modes)
-    std::vector<Word16> tc;      // tensor-core mode: MMA fragments and Q62 phases
+    std::vector<Word16> tc;      // tensor-core modes: block digits and Q62 phases
     bool is_tc = false;
+    bool tc_ok = true;           // every block's digit sums stay in the exact float32 range
 };
 
 // ---- tensor-core lowering ------------------------------------------------
@@ -241,12 +247,78 @@ void tc_fragments(int k, const std::vector<svp::cd>& M, std::vector<Word16>& out
                 }
 }
 
+// Balanced digits of a Q62 value for the tensor-memory kernel: v = q >> 6 =
+// sum_j d_j 256^(6 - j), d_0 = (v + 0x808080808080) >> 48, d_j = byte 6 - j
+// of v + 0x808080808080 minus 128 (so |d_0| <= 256, d_j in [-128, 127]).
+void balanced_digits(int64_t q, int (&d)[7]) {
+    const int64_t u = (q >> 6) + 0x808080808080ll;
+    d[0] = (int)(u >> 48);
+    for (int j = 1; j < 7; j++) d[j] = (int)((u >> (8 * (6 - j))) & 255) - 128;
+}
+
+// float16 bits of an integer |d| < 2^11 (exact).
+uint16_t f16_of_int(int d) {
+    if (d == 0) return 0;
+    const unsigned a = (unsigned)(d < 0 ? -d : d);
+    int e = 31 - __builtin_clz(a);  // 2^e <= a < 2^(e+1)
+    const unsigned mant = (a << (10 - e)) & 0x3FFu;
+    return (uint16_t)((d < 0 ? 0x8000u : 0u) | ((unsigned)(e + 15) << 10) | mant);
+}
+
+// Block digits in the shared-memory image the tcgen05 kernel copies: B is
+// 7R x R fp16, row j R + r' = digit j of real-form row r (r' = (amp >> 2) 8 +
+// part 4 + (amp & 3) for output part 0 = re / 1 = im of amplitude amp),
+// column c = real-form column; K-major core matrices of 8 rows x 16 bytes
+// (128 bytes between core matrices along K, 16 R bytes along N).  Returns
+// false if some level sum could exceed 2^22 in magnitude (amplitude digits
+// bounded by 256 for the top digit and 128 for the others).
+bool t05_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& out) {
+    const int D = 1 << k, R = 2 * D, SBO = 16 * R;
+    std::vector<uint16_t> img((size_t)7 * R * R, 0);
+    bool ok = true;
+    for (int r = 0; r < R; r++) {
+        const int part = r / D, amp = r % D;
+        const int rp = (amp >> 2) * 8 + part * 4 + (amp & 3);
+        int64_t S[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < R; c++) {
+            const svp::cd u = M[(size_t)amp * D + (c % D)];
+            double v;
+            if (part == 0) v = c < D ? u.real() : -u.imag();
+            else v = c < D ? u.imag() : u.real();
+            int d[7];
+            balanced_digits(q62_of(v), d);
+            for (int j = 0; j < 7; j++) {
+                S[j] += d[j] < 0 ? -d[j] : d[j];
+                const int n = j * R + rp;
+                const size_t off = (size_t)(n >> 3) * SBO + (size_t)(c >> 3) * 128 + (n & 7) * 16 + (c & 7) * 2;
+                img[off / 2] = f16_of_int(d[j]);
+            }
+        }
+        for (int L = 0; L < 7; L++) {
+            int64_t b = 0;
+            for (int i = 0; i <= L; i++) b += (i == 0 ? 256 : 128) * S[L - i];
+            if (b > (1ll << 22)) ok = false;
+        }
+    }
+    const size_t words = img.size() * 2 / sizeof(Word16);
+    const size_t at = out.size();
+    out.resize(at + words);
+    std::memcpy(out.data() + at, img.data(), img.size() * 2);
+    return ok;
+}
+
 void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE) {
     L.passes.clear();
     L.ops.clear();
     L.coef.clear();
     L.tc.clear();
-    L.is_tc = arith == SV_ARITH_TC;
+    L.is_tc = is_tc(arith);
+    L.tc_ok = true;
+    const bool t05 = arith == SV_ARITH_TC;
+    auto block_digits = [&](int k, const std::vector<svp::cd>& M) {
+        if (t05) L.tc_ok = t05_block_image(k, M, L.tc) && L.tc_ok;
+        else tc_fragments(k, M, L.tc);
+    };
     for (const auto& ps : P.passes) {
         DevPass dp;
         std::memset(&dp, 0, sizeof(dp));
@@ -295,9 +367,9 @@ void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE) {
                     extend_to3(b.k, op.pos, b.mat, avail, pos3, M3);
                     op.k = 3;
                     for (int j = 0; j < 3; j++) op.pos[j] = pos3[j];
-                    tc_fragments(3, M3, L.tc);
+                    block_digits(3, M3);
                 } else {
-                    tc_fragments(b.k, b.mat, L.tc);
+                    block_digits(b.k, b.mat);
                 }
             } else {
                 L.coef.insert(L.coef.end(), b.mat.begin(), b.mat.end());
@@ -366,9 +438,14 @@ size_t coef_bytes(const Lowered& L, int dt) {
     return L.is_tc ? L.tc.size() * sizeof(Word16) : L.coef.size() * coef_elem_bytes(dt);
 }
 
+// Internal status: a tensor-core block failed the exact-range check (the
+// caller re-plans in double-float arithmetic).
+constexpr int kRetryDF64 = 1;
+
 int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
     Lowered L;
     lower(P, L, arith);
+    if (!L.tc_ok) return kRetryDF64;
     const size_t ops_bytes = L.ops.size() * sizeof(DevOp);
     const size_t coef_off = align256(ops_bytes);
     const size_t ent_off = align256(coef_off + coef_bytes(L, s->dt));
@@ -410,6 +487,14 @@ int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
         if (timing) SV_TRY(cudaEventRecord(s->events[launches], s->stream));
     }
     SV_TRY(cudaStreamSynchronize(s->stream));
+    if (arith == SV_ARITH_TC) {
+        int fault = 0;
+        SV_TRY(svk::tc_fault_take(&fault));
+        if (fault) {
+            s->failed = true;
+            return SV_ERR_TIMEOUT;
+        }
+    }
     s->last.n_launches = launches;
     s->last.kernel_ms = 0;
     s->last.max_kernel_ms = 0;
@@ -546,7 +631,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     if (o && o->debug_checks && svp::check_plan(P, ng, g) != 0) return SV_ERR_STATE;
     const double t1 = now_ms();
     int arith = resolve_arith(s->dt, o, s->n);
-    if (arith == SV_ARITH_TC && s->foreign) {
+    if (is_tc(arith) && s->foreign) {
         // caller-supplied amplitudes: the fixed-point tile needs |re|, |im| <= 1
         SV_TRY(ensure(&s->d_red, &s->d_red_cap, 256, false));
         SV_TRY(svk::launch_max_abs_c128(s->amp, s->n, (unsigned long long*)s->d_red, s->stream, s->di));
@@ -564,6 +649,13 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
         P = plan_for(s->n, s->dt, g, ng, &df, max_tile(s->dt, s->di));
     }
     rc = apply_plan(s, P, arith, o && o->timing);
+    if (rc == kRetryDF64) {  // a block outside the digit scheme's exact range
+        sv_run_opts df = o ? *o : sv_run_opts{};
+        df.arith = SV_ARITH_DF64;
+        arith = SV_ARITH_DF64;
+        P = plan_for(s->n, s->dt, g, ng, &df, max_tile(s->dt, s->di));
+        rc = apply_plan(s, P, arith, o && o->timing);
+    }
     s->last.n_blocks = (int32_t)P.blocks.size();
     s->last.n_passes = (int32_t)P.passes.size();
     s->last.fuse_k = P.fuse_k;
@@ -571,7 +663,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     s->last.arith = arith;
     s->last.flops = P.flops;
     s->last.alu_ops = P.alu_ops;
-    s->last.tensor_flops = arith == SV_ARITH_TC ? P.mma_flops : 0.0;
+    s->last.tensor_flops = is_tc(arith) ? P.mma_flops : 0.0;
     s->last.hbm_bytes = 2.0 * (double)s->bytes * (double)P.passes.size();
     s->last.plan_ms = t1 - t0;
     return rc;
@@ -730,6 +822,13 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         bp.arith = resolve_arith(it.dt, opts, it.n_qubits);
         bp.plan = plan_for(it.n_qubits, it.dt, it.gates, it.n_gates, opts, max_tile(it.dt, b->di));
         lower(bp.plan, bp.low, bp.arith);
+        if (!bp.low.tc_ok) {  // a block outside the digit scheme's exact range: double-float
+            sv_run_opts df = opts ? *opts : sv_run_opts{};
+            df.arith = SV_ARITH_DF64;
+            bp.arith = SV_ARITH_DF64;
+            bp.plan = plan_for(it.n_qubits, it.dt, it.gates, it.n_gates, &df, max_tile(it.dt, b->di));
+            lower(bp.plan, bp.low, bp.arith);
+        }
         bp.host_out = !it.probs_on_device;
         P.push_back(std::move(bp));
     }
@@ -745,9 +844,13 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         bp.probs_off = off;
         off += align256(((size_t)8) << bp.n);
     }
-    // group by kernel mode (dtype, arithmetic)
+    // group by kernel mode (dtype, arithmetic): kBatchModes values of mode_of
+    constexpr int kBatchModes = 5;
     auto mode_of = [](const BatchItemPlan& bp) {
-        return bp.dt == SV_C64 ? 0 : (bp.arith == SV_ARITH_DF64 ? 2 : (bp.arith == SV_ARITH_TC ? 3 : 1));
+        if (bp.dt == SV_C64) return 0;
+        if (bp.arith == SV_ARITH_DF64) return 2;
+        if (bp.arith == SV_ARITH_TC) return 3;
+        return bp.arith == SV_ARITH_TC_SYNC ? 4 : 1;
     };
     std::vector<DevOp> ops;
     std::vector<unsigned char> coefs;  // per-mode coefficient blobs, concatenated
@@ -788,7 +891,7 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
     off += align256(coefs.size() + 16);
     // multi-state launches per (mode, pass index); the op/coef offsets inside each
     // entry's pass point at the item's ops; coefficient offsets are rebased below
-    for (int mode = 0; mode < 4; mode++) {
+    for (int mode = 0; mode < kBatchModes; mode++) {
         size_t max_passes = 0;
         std::vector<size_t> members;
         for (size_t i = 0; i < P.size(); i++)
@@ -855,7 +958,7 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
     for (auto& en : entries) en.state = (uint64_t)(uintptr_t)(A + P[(size_t)en.state].state_off);
     {
         size_t k = 0;
-        for (int mode = 0; mode < 4; mode++)
+        for (int mode = 0; mode < kBatchModes; mode++)
             for (size_t i = 0; i < P.size(); i++) {
                 if (mode_of(P[i]) != mode) continue;
                 sentries[k].state = (uint64_t)(uintptr_t)(A + P[i].state_off);
@@ -863,6 +966,7 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
                                                   : (uint64_t)(uintptr_t)items[P[i].idx].probs_out;
                 k++;
             }
+        if (k != sentries.size()) return fail(SV_ERR_STATE);  // every state entry has its addresses
     }
     for (auto& bp : P)
         if (bp.host_out)
@@ -940,6 +1044,9 @@ int sv_batch_execute(sv_batch* b) {
             cudaSuccess)
             return SV_ERR_CUDA;
     if (cudaStreamSynchronize(b->stream) != cudaSuccess) return SV_ERR_CUDA;
+    int fault = 0;
+    if (svk::tc_fault_take(&fault) != cudaSuccess) return SV_ERR_CUDA;
+    if (fault) return SV_ERR_TIMEOUT;
     float ms = 0;
     if (cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]) == cudaSuccess) b->last_ms = ms;
     return SV_OK;

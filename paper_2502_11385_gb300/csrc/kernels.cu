@@ -14,6 +14,8 @@
 // Amplitudes are interleaved complex; index bit q is qubit q.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "sv.h"
 
@@ -173,7 +175,7 @@ __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, cons
     }
 }
 
-// Diagonal ops visit amplitude i = threadIdx.x + it * kTileThreads.  The
+// Diagonal ops visit amplitude i = threadIdx.x + it * (CTA size).  The
 // phase-table index takes bit j from tile position pos[j] (or, for a
 // non-local qubit, from the tile's base index); the bits below log2 of the
 // CTA size come from the thread id and are gathered once per op.
@@ -184,10 +186,8 @@ struct DiagIndex {
     int sw_t;       // swizzle of the thread's part of i
 };
 
-template <typename SwzT>
+template <typename SwzT, int LT = 8>  // LT = log2 of the CTA size
 __device__ __forceinline__ DiagIndex diag_index(const DevOp& op, uint64_t tile_base) {
-    constexpr int LT = 8;  // log2(kTileThreads)
-    static_assert((1 << LT) == kTileThreads, "diag index split assumes 256 threads");
     DiagIndex d;
     d.idx_t = 0;
     d.nh = 0;
@@ -211,13 +211,13 @@ __device__ __forceinline__ DiagIndex diag_index(const DevOp& op, uint64_t tile_b
     return d;
 }
 
-template <typename SwzT>
+template <typename SwzT, int LT = 8>
 __device__ __forceinline__ void diag_at(const DiagIndex& d, int it, int& idx, int& sidx) {
     idx = d.idx_t;
 #pragma unroll
     for (int j = 0; j < 5; j++)
         if (j < d.nh) idx |= ((it >> d.hp[j]) & 1) << d.hb[j];
-    sidx = d.sw_t ^ swz<SwzT>(it << 8);
+    sidx = d.sw_t ^ swz<SwzT>(it << LT);
 }
 
 template <typename R>
@@ -632,16 +632,17 @@ __device__ __forceinline__ long long qmul(long long a, long long b) {
     return (long long)(((unsigned long long)hi << 2) | (lo >> 62));
 }
 
+template <int LT = 8>  // log2 of the CTA size
 __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const Q2* __restrict__ M,
                                            uint64_t tile_base) {
-    const DiagIndex d = diag_index<double>(op, tile_base);
+    const DiagIndex d = diag_index<double, LT>(op, tile_base);
     const int N = 1 << m;
-    const int iters = (N + 255) >> 8;
+    const int iters = (N + (1 << LT) - 1) >> LT;
     const bool sign_only = op.flags & OPF_SIGN_ONLY;
     for (int it = 0; it < iters; it++) {
-        if ((int)threadIdx.x + (it << 8) >= N) break;
+        if ((int)threadIdx.x + (it << LT) >= N) break;
         int idx, si;
-        diag_at<double>(d, it, idx, si);
+        diag_at<double, LT>(d, it, idx, si);
         const Q2 u = M[idx];
         const Q2 a = sm[si];
         if (sign_only) {
@@ -653,9 +654,293 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
 }
 
 // ---------------------------------------------------------------------------
-// K5: the tile-pass kernel, shared by the three arithmetic modes.
+// K5-t05: the same digit products on the fifth-generation tensor cores
+// (tcgen05.mma issued by one thread, operands in shared memory, accumulators
+// in tensor memory).
+//
+// Digits are balanced here: v = x >> 6 = sum_j X_j 256^(6 - j) with
+// |X_0| <= 256 and X_j in [-128, 127] for j >= 1 (the bytes of
+// v + 0x808080808080, minus 128), and held as float16, exact for integers
+// below 2^11: one byte permute and one logic op place two bytes b in the
+// mantissas of 1024 + b, one packed half subtraction removes 1024 + 128.  For
+// a unitary block every level sum then stays below 2^21.5 (the host checks
+// the bound 2^22 per block), so a level becomes an integer with one float
+// add: the bits of z + 1.5 * 2^23 are 0x4B400000 + z.
+//
+// One round covers 128 groups (one M = 128 tile; 3-qubit blocks take two
+// M-tiles per round):
+//   A_i (shared, 128 x R fp16) = digit i of the groups' R = 2^(k+1) real
+//       components, K-major core matrices of 8 rows x 16 bytes, no swizzle;
+//   B   (shared, 7R x R fp16): row j R + r' = digit j of real-form row r of
+//       the block (r' = (amp >> 2) 8 + part 4 + (amp & 3) for output
+//       component part (0 = re, 1 = im) of amplitude amp, so that one thread
+//       reads the re and im outputs of 4 amplitudes from 8 adjacent columns);
+//   D   (tensor memory, 128 lanes x 7R fp32 columns): column L R + r' =
+//       level L of output r'.
+// Amplitude digit i meets block digits j = 0..6-i in one MMA of
+// N = (7 - i) R whose accumulator starts at column i R, so each level i + j
+// collects in its own columns: 7 x R/16 MMAs per M-tile and round.  Two
+// accumulator buffers (2 x 256 TMEM columns, one CTA per SM) let the MMAs of
+// round r run while the threads re-assemble round r - 1; the CTA has 512
+// threads (16 warps) to hide the latency of the digit work.
 // ---------------------------------------------------------------------------
-enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2, MODE_TC = 3 };
+namespace t05 {
+
+constexpr int kThreads = 512;
+constexpr int kLogThreads = 9;
+constexpr int kABytes = 7 * 128 * 32 * 2;  // 7 digit planes of 128 x 32 fp16 (or 2 M-tiles x 7 x 128 x 16)
+constexpr int kBBytes = 14 * 32 * 32;      // 7R x R fp16 for R = 32
+constexpr int kSmemBase = kABytes + kBBytes;  // 70 KiB; the amplitude tile follows
+constexpr int kSmemMin = 116 * 1024;       // one CTA per SM (it holds all 512 TMEM columns)
+constexpr int kTmemCols = 512;             // two accumulator buffers
+constexpr uint32_t kTmemBuf = 256;         // column offset of the second buffer
+constexpr unsigned kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
+constexpr int kWaitSpins = 1 << 20;
+
+__device__ int g_fault;  // set when a bounded wait ran out (read and cleared by the host)
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (K-major, no swizzle): start address, byte
+// step between core matrices along K (lbo) and along M / N (sbo), version 1.
+__device__ __forceinline__ uint64_t desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: f32 accumulator, f16 A and B, both
+// K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc(int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t id, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(id), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+                 : "memory");
+}
+
+// Waits for the phase of the given parity to complete; false after kWaitSpins
+// polls (the caller reports SV_ERR_TIMEOUT instead of hanging).
+__device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
+    for (int it = 0; it < kWaitSpins; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// 8 consecutive fp32 columns of this warp's 32 TMEM lanes
+__device__ __forceinline__ void ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ unsigned sub_h2(unsigned a, unsigned b) {
+    unsigned d;
+    asm("sub.rn.f16x2 %0, %1, %2;\n" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+// Byte k of w0 and of w1 as balanced fp16 digits (b - 128), packed.
+template <int K8>
+__device__ __forceinline__ unsigned h2_byte_pair(unsigned w0, unsigned w1) {
+    constexpr unsigned sel = K8 | (K8 << 4) | ((4 + K8) << 8) | ((4 + K8) << 12);
+    const unsigned t = (__byte_perm(w0, w1, sel) & 0x00FF00FFu) | 0x64006400u;  // fp16 1024 + byte, twice
+    return sub_h2(t, 0x64806480u);                                            // minus 1024 + 128
+}
+
+// The seven balanced digits of two Q62 values, packed pairwise as fp16 x 2.
+__device__ __forceinline__ void bal_digits_pair(long long x0, long long x1, unsigned (&o)[7]) {
+    const long long u0 = (x0 >> 6) + 0x808080808080ll, u1 = (x1 >> 6) + 0x808080808080ll;
+    const unsigned lo0 = (unsigned)u0, hi0 = (unsigned)((unsigned long long)u0 >> 32);
+    const unsigned lo1 = (unsigned)u1, hi1 = (unsigned)((unsigned long long)u1 >> 32);
+    // top digit d (|d| <= 256): fp16 bits of 1536 + d are 0x6600 + d
+    const unsigned t0 = 0x6600u + (unsigned)((int)hi0 >> 16), t1 = 0x6600u + (unsigned)((int)hi1 >> 16);
+    o[0] = sub_h2(__byte_perm(t0, t1, 0x5410), 0x66006600u);
+    o[1] = h2_byte_pair<1>(hi0, hi1);  // byte 5 of u
+    o[2] = h2_byte_pair<0>(hi0, hi1);  // byte 4
+    o[3] = h2_byte_pair<3>(lo0, lo1);
+    o[4] = h2_byte_pair<2>(lo0, lo1);
+    o[5] = h2_byte_pair<1>(lo0, lo1);
+    o[6] = h2_byte_pair<0>(lo0, lo1);
+}
+
+// Digits of 4 consecutive components of one row into the 7 digit planes
+// (8 bytes per plane: half a core-matrix row).
+__device__ __forceinline__ void store_digits4(long long x0, long long x1, long long x2, long long x3,
+                                              unsigned char* p, int plane_bytes) {
+    unsigned d01[7], d23[7];
+    bal_digits_pair(x0, x1, d01);
+    bal_digits_pair(x2, x3, d23);
+#pragma unroll
+    for (int i = 0; i < 7; i++) *reinterpret_cast<uint2*>(p + i * plane_bytes) = make_uint2(d01[i], d23[i]);
+}
+
+struct Ctx {
+    unsigned char* a;  // digit planes
+    unsigned char* b;  // block digits
+    uint32_t a_addr, b_addr, mbar, tmem;
+    uint32_t phase;
+    bool failed;
+};
+
+// Dense block of 3 or 4 qubits on tcgen05 (balanced 8-bit digits, levels 0..6).
+// Bg: the block's digits in the shared-memory image (14 R^2 bytes).
+template <int K>
+__device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const uint4* __restrict__ Bg, Ctx& cx) {
+    static_assert(K == 3 || K == 4, "tensor-core blocks have 3 or 4 qubits");
+    constexpr int D = 1 << K, R = 2 * D;
+    constexpr int SBO = 16 * R;         // bytes between 8-row core groups (R / 8 core matrices of 128 B)
+    constexpr int PLANE = 128 * R * 2;  // one digit plane of one M-tile
+    constexpr int GPR = K == 3 ? 256 : 128;  // groups per round
+    int pos[K], pm[K];
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        pos[j] = op.pos[j];
+        pm[j] = 1 << pos[j];
+    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // block digits: asynchronous copies, overlapped with the first digit split
+    for (int i = tid; i < 14 * R * R / 16; i += kThreads) cp_async16(cx.b_addr + 16 * i, Bg + i);
+    const int ng = 1 << (m - K);
+    // digit split: thread -> (M-tile, row, amplitude quartet qa); lane pairs
+    // share a row so that a warp's 8-byte stores fill whole core-matrix rows
+    const int s_row = ((tid >> 5) & 7) * 16 + (lane >> 1);
+    const int s_mt = K == 4 ? 0 : tid >> 8;
+    const int s_qa = K == 4 ? 2 * (tid >> 8) + (lane & 1) : (lane & 1);
+    // re-assembly: warp -> (TMEM lane quarter, M-tile, column group of 8 = 4 amplitudes)
+    const int e_cg = K == 4 ? warp >> 2 : (warp >> 2) & 1;
+    const int e_mt = K == 4 ? 0 : warp >> 3;
+    const int e_row = (warp & 3) * 32 + lane;
+    // re-assembly of the round starting at group r0 from TMEM buffer tbuf
+    auto reassemble = [&](int r0, int r_mt, uint32_t tbuf) {
+        fence_after();
+        if (e_mt >= r_mt) return;  // warp-uniform
+        const uint32_t t0 = cx.tmem + tbuf + ((uint32_t)((warp & 3) * 32) << 16) + e_mt * 128 + 8 * e_cg;
+        // level words w_L = bits of (Z_L + 1.5 * 2^23) = 0x4B400000 + Z_L; pairs
+        // P = 256 Z_a + Z_b fit in int32 (|Z| <= 2^22), formed with wrapping
+        // 32-bit arithmetic: 256 w_a + w_b - 257 * 0x4B400000
+        constexpr unsigned kPairBias = 0u - 257u * kMagicBits;
+        int P[3][8];
+        uint32_t a[8], b[8];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            ld8(t0 + (2 * q) * R, a);
+            ld8(t0 + (2 * q + 1) * R, b);
+            ld_wait();
+#pragma unroll
+            for (int e = 0; e < 8; e++) {
+                const unsigned w0 = __float_as_uint(__uint_as_float(a[e]) + 12582912.0f);
+                const unsigned w1 = __float_as_uint(__uint_as_float(b[e]) + 12582912.0f);
+                P[q][e] = (int)(w0 * 256u + w1 + kPairBias);
+            }
+        }
+        ld8(t0 + 6 * R, a);
+        ld_wait();
+        const int G = r0 + e_mt * 128 + e_row;
+        if (G < ng) {
+            const int bg = swz<double>(insert_zero_bits<K>(G, pos));
+            // y = 2^6 (P01 2^32 + P23 2^16 + P45) + Z_6 / 4 (rounded), in Q62 units
+            auto out = [&](int e) {
+                const int t6 = (int)(__float_as_uint(__uint_as_float(a[e]) + 12582912.0f) - kMagicBits + 2u) >> 2;
+                return (long long)(((unsigned long long)(long long)P[0][e] << 38) +
+                                   ((unsigned long long)(long long)P[1][e] << 22) +
+                                   ((unsigned long long)(long long)P[2][e] << 6) +
+                                   (unsigned long long)(long long)t6);
+            };
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                sm[bg ^ swz<double>(group_offset<K>(4 * e_cg + e, pm))] = Q2{out(e), out(e + 4)};
+        }
+    };
+    // Rounds are pipelined over two TMEM accumulators: the MMAs of round r
+    // run while the threads re-assemble round r - 1.
+    int prev_g0 = -1, prev_mt = 0;
+    uint32_t prev_buf = 0;
+    for (int g0 = 0; g0 < ng; g0 += GPR) {
+        {
+            const int G = g0 + s_mt * 128 + s_row;
+            if (G < ng) {
+                const int bg = swz<double>(insert_zero_bits<K>(G, pos));
+                Q2 v[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) v[e] = sm[bg ^ swz<double>(group_offset<K>(4 * s_qa + e, pm))];
+                // component k = part D + 4 qa + e: k-core k >> 3, byte (k & 7) * 2
+                unsigned char* row0 = cx.a + s_mt * 7 * PLANE + (s_row >> 3) * SBO + (s_row & 7) * 16 + (s_qa & 1) * 8;
+                store_digits4(v[0].re, v[1].re, v[2].re, v[3].re, row0 + (s_qa >> 1) * 128, PLANE);
+                store_digits4(v[0].im, v[1].im, v[2].im, v[3].im, row0 + (D / 8 + (s_qa >> 1)) * 128, PLANE);
+            }
+        }
+        cp_async_wait_all();
+        fence_async_smem();
+        __syncthreads();
+        const int n_mt = (K == 3 && g0 + 128 < ng) ? 2 : 1;
+        const uint32_t buf = (uint32_t)((g0 / GPR) & 1) * kTmemBuf;
+        if (tid == 0) {
+            fence_after();
+            for (int mt = 0; mt < n_mt; mt++)
+#pragma unroll
+                for (int i = 0; i < 7; i++)
+#pragma unroll
+                    for (int ks = 0; ks < R / 16; ks++) {
+                        const uint64_t da = desc(cx.a_addr + (mt * 7 + i) * PLANE + ks * 256, 128, SBO);
+                        const uint64_t db = desc(cx.b_addr + ks * 256, 128, SBO);
+                        mma(cx.tmem + buf + mt * 128 + i * R, da, db, idesc((7 - i) * R), (i | ks) != 0);
+                    }
+            commit(cx.mbar);
+        }
+        if (prev_g0 >= 0) reassemble(prev_g0, prev_mt, prev_buf);
+        const bool ok = wait(cx.mbar, cx.phase);
+        cx.phase ^= 1;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(&g_fault, 1);
+            wait(cx.mbar, cx.phase ^ 1);  // give the MMAs in flight one more bounded wait
+            cx.failed = true;
+            return;
+        }
+        fence_before();
+        __syncthreads();
+        prev_g0 = g0;
+        prev_mt = n_mt;
+        prev_buf = buf;
+    }
+    reassemble(prev_g0, prev_mt, prev_buf);
+    fence_before();
+    __syncthreads();
+}
+
+}  // namespace t05
+
+// ---------------------------------------------------------------------------
+// K5: the tile-pass kernel, shared by the arithmetic modes.
+// ---------------------------------------------------------------------------
+enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2, MODE_TC = 3, MODE_T05 = 4 };
 
 template <int MODE>
 struct TileTraits;
@@ -685,6 +970,13 @@ struct TileTraits<MODE_TC> {
     using Store = Cx<double>;
     using Smem = Q2;
     using Coef = uint4;  // dense: MMA fragments; diagonal: Q2 entries
+    using SwzT = double;
+};
+template <>
+struct TileTraits<MODE_T05> {
+    using Store = Cx<double>;
+    using Smem = Q2;
+    using Coef = uint4;  // dense: block digits in their shared-memory image; diagonal: Q2 entries
     using SwzT = double;
 };
 
@@ -736,18 +1028,49 @@ __device__ __forceinline__ void apply_op(typename TileTraits<MODE>::Smem* sm, in
 // apply the pass's ops in order, scatter the tile back.  Persistent: each CTA
 // strides over the flattened tile space of all entries.
 template <int MODE, int KMAX>
-__global__ void __launch_bounds__(kTileThreads, MODE == MODE_TC ? 2 : 1)
+__global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThreads,
+                                  MODE == MODE_TC ? 2 : 1)
     k_tile_pass(const BatchEntry* __restrict__ E, int n_entries, uint64_t total_tiles, const DevOp* __restrict__ ops,
                 const typename TileTraits<MODE>::Coef* __restrict__ coef) {
     using Tr = TileTraits<MODE>;
     using Store = typename Tr::Store;
     using Smem = typename Tr::Smem;
     using SwzT = typename Tr::SwzT;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    Smem* sm = reinterpret_cast<Smem*>(smraw);
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    // tcgen05 mode: digit planes and block digits first, the tile after them
+    Smem* sm = reinterpret_cast<Smem*>(smraw + (MODE == MODE_T05 ? t05::kSmemBase : 0));
     __shared__ uint64_t dep[2][32];  // deposit tables for the tile's high local bits
     __shared__ __align__(16) DevPass P;
     __shared__ uint64_t s_state, s_begin;
+    __shared__ __align__(8) uint64_t t05_mbar;
+    __shared__ uint32_t t05_tmem;
+    constexpr int kOpCache = 48;  // the pass's op descriptors, read once per pass
+    __shared__ DevOp s_ops[kOpCache];
+    t05::Ctx cx{};
+    if constexpr (MODE == MODE_T05) {
+        if (threadIdx.x < 32) {  // warp 0 owns the tensor-memory allocation
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                             t05::smem_addr(&t05_tmem)),
+                         "r"(t05::kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+        }
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(t05::smem_addr(&t05_mbar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
+        t05::fence_before();
+        __syncthreads();
+        t05::fence_after();
+        cx.a = smraw;
+        cx.b = smraw + t05::kABytes;
+        cx.a_addr = t05::smem_addr(cx.a);
+        cx.b_addr = t05::smem_addr(cx.b);
+        cx.mbar = t05::smem_addr(&t05_mbar);
+        cx.tmem = t05_tmem;
+        cx.phase = 0;
+        cx.failed = false;
+    }
     int cur = -1;
     for (uint64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
         int lo = 0, hi = n_entries - 1;  // entry owning tile t (uniform across the CTA)
@@ -766,6 +1089,11 @@ __global__ void __launch_bounds__(kTileThreads, MODE == MODE_TC ? 2 : 1)
                 s_begin = E[lo].tile_begin;
             }
             __syncthreads();
+            if (P.n_ops <= kOpCache) {
+                const int4* osrc = reinterpret_cast<const int4*>(ops + P.op0);
+                int4* odst = reinterpret_cast<int4*>(s_ops);
+                for (int i = threadIdx.x; i < P.n_ops * (int)(sizeof(DevOp) / 16); i += blockDim.x) odst[i] = osrc[i];
+            }
             if (threadIdx.x < 64) {
                 const int w = threadIdx.x >> 5, v = threadIdx.x & 31, hb = P.m - P.c;
                 uint64_t d = 0;
@@ -796,7 +1124,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == MODE_TC ? 2 : 1)
                 d2df(a.im, v.ih, v.il);
                 sm[swz<double>(j)] = v;
             }
-        } else if constexpr (MODE == MODE_TC) {
+        } else if constexpr (MODE == MODE_TC || MODE == MODE_T05) {
             const int N = 1 << m;
             for (int j = threadIdx.x; j < N; j += blockDim.x) {
                 const int r = j >> c;
@@ -817,9 +1145,20 @@ __global__ void __launch_bounds__(kTileThreads, MODE == MODE_TC ? 2 : 1)
         __syncthreads();
         const int n_ops = P.n_ops, op0 = P.op0;
         for (int o = 0; o < n_ops; o++) {
-            const DevOp op = ops[op0 + o];
-            apply_op<MODE, KMAX>(sm, m, op, coef + op.coeff, base);
+            const DevOp op = n_ops <= kOpCache ? s_ops[o] : ops[op0 + o];
+            if constexpr (MODE == MODE_T05) {
+                if (op.kind == OP_DIAG)
+                    op_diag_tc<t05::kLogThreads>(sm, m, op, reinterpret_cast<const Q2*>(coef + op.coeff), base);
+                else if (op.k <= 3) t05::op_dense<3>(sm, m, op, coef + op.coeff, cx);
+                else t05::op_dense<(KMAX >= 4 ? 4 : 3)>(sm, m, op, coef + op.coeff, cx);  // capped at 4 qubits
+                if (cx.failed) break;  // uniform: decided by a block-wide vote
+            } else {
+                apply_op<MODE, KMAX>(sm, m, op, coef + op.coeff, base);
+            }
             __syncthreads();
+        }
+        if constexpr (MODE == MODE_T05) {
+            if (cx.failed) break;  // the state is left undefined; the host reports SV_ERR_TIMEOUT
         }
         if constexpr (MODE == MODE_DF) {
             const int N = 1 << m;
@@ -829,7 +1168,7 @@ __global__ void __launch_bounds__(kTileThreads, MODE == MODE_TC ? 2 : 1)
                 const DF4 v = sm[swz<double>(j)];
                 st[gidx] = Cx<double>{df2d(v.rh, v.rl), df2d(v.ih, v.il)};
             }
-        } else if constexpr (MODE == MODE_TC) {
+        } else if constexpr (MODE == MODE_TC || MODE == MODE_T05) {
             const int N = 1 << m;
             for (int j = threadIdx.x; j < N; j += blockDim.x) {
                 const int r = j >> c;
@@ -848,6 +1187,16 @@ __global__ void __launch_bounds__(kTileThreads, MODE == MODE_TC ? 2 : 1)
             }
         }
         __syncthreads();
+    }
+    if constexpr (MODE == MODE_T05) {
+        t05::fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            t05::fence_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(cx.tmem),
+                         "r"(t05::kTmemCols)
+                         : "memory");
+        }
     }
 }
 
@@ -1057,21 +1406,28 @@ template <int MODE, int KMAX>
 static cudaError_t tile_pass_impl(const BatchEntry* d_entries, int n_entries, uint64_t total_tiles, int max_m,
                                   const DevOp* d_ops, const void* d_coef, cudaStream_t s, const DevInfo& di) {
     using Tr = TileTraits<MODE>;
-    const size_t smem = ((size_t)1 << max_m) * sizeof(typename Tr::Smem);
+    size_t smem = ((size_t)1 << max_m) * sizeof(typename Tr::Smem);
+    if (MODE == MODE_T05) smem = std::max<size_t>(smem + t05::kSmemBase, t05::kSmemMin);
     static int configured_dev = -1;
+    static size_t dyn_max = 0;
     if (configured_dev != di.device) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_pass<MODE, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(di.smem_optin - 2048));
+        cudaFuncAttributes fa{};
+        cudaError_t e = cudaFuncGetAttributes(&fa, k_tile_pass<MODE, KMAX>);
+        if (e != cudaSuccess) return e;
+        dyn_max = di.smem_optin - fa.sharedSizeBytes;  // opt-in limit minus the kernel's static shared memory
+        e = cudaFuncSetAttribute(k_tile_pass<MODE, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
         if (e != cudaSuccess) return e;
         configured_dev = di.device;
     }
+    if (smem > dyn_max) return cudaErrorInvalidValue;
+    const int threads = MODE == MODE_T05 ? t05::kThreads : kTileThreads;
     int per_sm = 1;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<MODE, KMAX>, kTileThreads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<MODE, KMAX>, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     uint64_t grid = (uint64_t)di.sms * per_sm;
     if (grid > total_tiles) grid = total_tiles;
-    k_tile_pass<MODE, KMAX><<<(unsigned)grid, kTileThreads, smem, s>>>(
+    k_tile_pass<MODE, KMAX><<<(unsigned)grid, threads, smem, s>>>(
         d_entries, n_entries, total_tiles, d_ops, (const typename Tr::Coef*)d_coef);
     return cudaGetLastError();
 }
@@ -1098,6 +1454,8 @@ cudaError_t launch_tile_pass(int dt, int arith, const BatchEntry* d_entries, int
     if (arith == SV_ARITH_DF64)
         return tile_pass_mode<MODE_DF>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
     if (arith == SV_ARITH_TC)
+        return tile_pass_mode<MODE_T05>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
+    if (arith == SV_ARITH_TC_SYNC)
         return tile_pass_mode<MODE_TC>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
     return tile_pass_mode<MODE_F64>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
 }
@@ -1118,6 +1476,13 @@ cudaError_t launch_probs_multi(int dt, const StateEntry* d_entries, int n_entrie
     if (dt == SV_C64) k_probs_multi<float><<<grid, 256, 0, s>>>(d_entries, n_entries);
     else k_probs_multi<double><<<grid, 256, 0, s>>>(d_entries, n_entries);
     return cudaGetLastError();
+}
+
+cudaError_t tc_fault_take(int* fault) {
+    int zero = 0;
+    cudaError_t e = cudaMemcpyFromSymbol(fault, t05::g_fault, sizeof(int));
+    if (e == cudaSuccess && *fault) e = cudaMemcpyToSymbol(t05::g_fault, &zero, sizeof(int));
+    return e;
 }
 
 cudaError_t launch_max_abs_c128(const void* amp, int n, unsigned long long* d_out, cudaStream_t s,

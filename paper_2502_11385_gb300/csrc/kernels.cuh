@@ -25,8 +25,8 @@ cudaError_t launch_init(int dt, void* amp, int n, uint64_t basis, cudaStream_t s
 // memory: every tile of every entry is gathered into shared memory, the
 // entry's ops are applied in order, and the tile is written back.
 // total_tiles = sum of the entries' tile counts; max_m / kmax = largest tile
-// and dense block among the entries; arith: SV_ARITH_NATIVE or SV_ARITH_DF64
-// (complex128 only).
+// and dense block among the entries; arith: SV_ARITH_NATIVE, SV_ARITH_DF64,
+// SV_ARITH_TC or SV_ARITH_TC_SYNC (complex128 only).
 cudaError_t launch_tile_pass(int dt, int arith, const BatchEntry* d_entries, int n_entries, uint64_t total_tiles,
                              int max_m, int kmax, const DevOp* d_ops, const void* d_coef, cudaStream_t s,
                              const DevInfo& di);
@@ -36,6 +36,10 @@ cudaError_t launch_init_multi(int dt, const StateEntry* d_entries, int n_entries
                               cudaStream_t s, const DevInfo& di);
 cudaError_t launch_probs_multi(int dt, const StateEntry* d_entries, int n_entries, uint64_t total_amps,
                                cudaStream_t s, const DevInfo& di);
+
+// Reads and clears the tensor-memory mode's fault flag (set when a bounded
+// wait for the tensor cores ran out; the launch then left its state undefined).
+cudaError_t tc_fault_take(int* fault);
 
 // *d_out = bit pattern of max |re|, |im| over a complex128 state.
 cudaError_t launch_max_abs_c128(const void* amp, int n, unsigned long long* d_out, cudaStream_t s,

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libsv.so")
 SV_OK, SV_ERR_ARG, SV_ERR_QUBIT, SV_ERR_OOM, SV_ERR_SIZE, SV_ERR_CUDA, SV_ERR_TIMEOUT, SV_ERR_STATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 C64, C128 = 0, 1
-ARITH_AUTO, ARITH_NATIVE, ARITH_DF64, ARITH_TC = 0, 1, 2, 3
+ARITH_AUTO, ARITH_NATIVE, ARITH_DF64, ARITH_TC, ARITH_TC_SYNC = 0, 1, 2, 3, 4
 DTYPES = {"c64": C64, "c128": C128, C64: C64, C128: C128}
 NP_DTYPE = {C64: np.complex64, C128: np.complex128}
 

@@ -295,7 +295,7 @@ def test_batch_matches_solo_bitwise_and_oracle(sv):
     for i, (n, dt) in enumerate(specs):
         g = _random_circuit(n, 60 + 5 * i, 400 + i)
         items.append((n, dt, g, None))
-    for arith in (sv.ARITH_NATIVE, sv.ARITH_DF64, sv.ARITH_TC):
+    for arith in (sv.ARITH_NATIVE, sv.ARITH_DF64, sv.ARITH_TC, sv.ARITH_TC_SYNC):
         opts = sv.run_opts(arith=arith)
         with sv.Batch(items, opts) as b:
             assert b.status == [0] * len(items)
@@ -384,25 +384,48 @@ def test_cut_variants_shared_work_matches_plain(sv, dtype):
 
 
 # ---------------------------------------------------------------------------
-# complex128 on the tensor cores (SV_ARITH_TC: exact digit split)
+# complex128 on the tensor cores: SV_ARITH_TC (tcgen05, accumulators in
+# tensor memory, balanced digits) and SV_ARITH_TC_SYNC (warp-level mma.sync)
 # ---------------------------------------------------------------------------
-def test_tc_brickwork12(sv):
+TC_MODES = ("tc", "tc_sync")
+
+
+def _tc_arith(sv, mode):
+    return sv.ARITH_TC if mode == "tc" else sv.ARITH_TC_SYNC
+
+
+@pytest.mark.parametrize("mode", TC_MODES)
+def test_tc_brickwork12(sv, mode):
     g = W.workload_brickwork12()
     ref = oracle.run(12, g)
     for k in (1, 3, 4, 5):
-        st = _check(sv, 12, "c128", g, ref, max_fuse_k=k, arith=sv.ARITH_TC)
-        assert st["arith"] == sv.ARITH_TC
+        st = _check(sv, 12, "c128", g, ref, max_fuse_k=k, arith=_tc_arith(sv, mode))
+        assert st["arith"] == _tc_arith(sv, mode)
 
 
+@pytest.mark.parametrize("mode", TC_MODES)
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("n,tile", [(9, 0), (16, 9), (20, 0)])
-def test_tc_random_circuits(sv, n, tile, k):
+def test_tc_random_circuits(sv, n, tile, k, mode):
     g = _random_circuit(n, 120, 9000 * n + k)
-    _check(sv, n, "c128", g, max_fuse_k=k, tile_qubits=tile, arith=sv.ARITH_TC)
+    _check(sv, n, "c128", g, max_fuse_k=k, tile_qubits=tile, arith=_tc_arith(sv, mode))
 
 
+@pytest.mark.parametrize("tile", [9, 10, 11, 12, 13])
+def test_tc_tile_sizes(sv, tile):
+    """tcgen05 mode across tile sizes: partial M-tiles (9, 10), two CTAs per SM
+    (11), one (12, 13)."""
+    n = 17
+    g = _random_circuit(n, 150, 31 + tile)
+    ref = oracle.run(n, g)
+    for k in (3, 4):
+        st = _check(sv, n, "c128", g, ref, max_fuse_k=k, tile_qubits=tile, arith=sv.ARITH_TC)
+        assert st["tile_qubits"] == tile and st["arith"] == sv.ARITH_TC
+
+
+@pytest.mark.parametrize("mode", TC_MODES)
 @pytest.mark.parametrize("n", [8, 12])
-def test_tc_every_gate_on_every_operand(sv, n):
+def test_tc_every_gate_on_every_operand(sv, n, mode):
     prep = _random_circuit(n, 3 * n, 27 + n, ops=[W.U3, W.CX])
     rows = []
     for op in range(14):
@@ -414,7 +437,27 @@ def test_tc_every_gate_on_every_operand(sv, n):
     g = W.concat(prep, W.gates(rows))
     ref = oracle.run(n, g)
     for k in (1, 3, 4, 5):
-        _check(sv, n, "c128", g, ref, max_fuse_k=k, arith=sv.ARITH_TC)
+        _check(sv, n, "c128", g, ref, max_fuse_k=k, arith=_tc_arith(sv, mode))
+
+
+def test_tc_basis_states_and_extreme_amplitudes(sv):
+    """Components of magnitude exactly 1 (basis states, permutations, signs)
+    sit at the edge of the fixed-point range: X/CX/SWAP/Z networks keep every
+    amplitude at 0 or +-1, and the result must be exact."""
+    n = 13
+    rng = np.random.default_rng(12)
+    rows = []
+    for _ in range(200):
+        op = int(rng.choice([W.X, W.Y, W.Z, W.CX, W.CZ, W.SWAP]))
+        q0 = int(rng.integers(n))
+        q1 = int(rng.choice([q for q in range(n) if q != q0])) if op >= W.CX else -1
+        rows.append((op, q0, q1))
+    g = W.gates(rows)
+    ref = oracle.run(n, g)
+    for k in (1, 3, 4):
+        amp, _, _, st = _run(sv, n, "c128", g, max_fuse_k=k, arith=sv.ARITH_TC)
+        assert st["arith"] == sv.ARITH_TC
+        assert np.array_equal(amp, ref), np.abs(amp - ref).max()
 
 
 def test_tc_small_states_fall_back(sv):
