@@ -443,35 +443,33 @@ struct alignas(16) Q2 {
     long long re, im;
 };
 
+// float64 -> fixed point with FB fraction bits (x * 2^FB truncated toward
+// zero), for |x| < 2^(62 - FB) (components of a normalised state): the
+// significand with its implicit bit is placed at bits 62..10 and shifted
+// right by 1023 - exponent + 62 - FB; zero and subnormal inputs (shift
+// clamped at 63) give 0.  Branch-free.
+template <int FB = 62>
 __device__ __forceinline__ long long d2q(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e == 0) return 0;
-    const unsigned long long m = (b & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = e - 1013;  // x * 2^62 = m * 2^(e - 1013)
-    long long v;
-    if (sh > 10) v = 0x7FFFFFFFFFFFFFFFll;  // |x| >= 2: outside the fixed-point range (saturated)
-    else if (sh >= 0) v = (long long)(m << sh);
-    else if (sh > -64) v = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
-    else v = 0;
-    return (b >> 63) ? -v : v;
+    const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+    const int s = min(max(1023 + 62 - FB - (int)((hi >> 20) & 0x7FFu), 0), 63);
+    const unsigned mh = (__funnelshift_l(lo, hi, 10) & 0x3FFFFFFFu) | 0x40000000u;
+    const long long v = (long long)((((unsigned long long)mh << 32) | (unsigned long long)(lo << 10)) >> s);
+    return (int)hi < 0 ? -v : v;
 }
 
+// Fixed point with FB fraction bits -> float64, truncated toward zero: |q|
+// normalised by its leading-zero count, the 52 bits below the leading one
+// form the fraction.
+template <int FB = 62>
 __device__ __forceinline__ double q2d(long long q) {
-    if (q == 0) return 0.0;
     const unsigned long long sign = (unsigned long long)q & 0x8000000000000000ull;
-    const unsigned long long a = sign ? (unsigned long long)(-q) : (unsigned long long)q;
+    const unsigned long long a = sign ? 0ull - (unsigned long long)q : (unsigned long long)q;
     const int lz = __clzll((long long)a);
-    const unsigned long long n = a << lz;  // leading one at bit 63
-    unsigned long long mant = n >> 11;
-    const unsigned long long rem = n & 0x7FFull;
-    if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) mant++;  // round to nearest even
-    unsigned long long E = (unsigned long long)(1023 + 1 - lz);      // value = a * 2^-62
-    if (mant >> 53) {
-        mant >>= 1;
-        E++;
-    }
-    return __longlong_as_double((long long)(sign | (E << 52) | (mant & ((1ull << 52) - 1))));
+    const unsigned long long n = a << (lz & 63);                      // leading one at bit 63 (a != 0)
+    const unsigned long long E = (unsigned long long)(1086 - FB - lz);  // value = a * 2^-FB
+    const unsigned long long bits = sign | (E << 52) | ((n >> 11) & ((1ull << 52) - 1));
+    return __longlong_as_double(a ? (long long)bits : 0ll);
 }
 
 __device__ __forceinline__ void mma_bf16_16816(float (&c)[4], const uint4& a, unsigned b0, unsigned b1) {
@@ -625,7 +623,8 @@ __device__ __forceinline__ void op_dense_tc(Q2* sm, int m, const DevOp& op, cons
     }
 }
 
-// Q62 x Q62 -> Q62 (floor)
+// (a * b) >> 62, floor: Q62 x Q62 -> Q62, or a Q62 phase times a Q56
+// amplitude -> Q56
 __device__ __forceinline__ long long qmul(long long a, long long b) {
     const long long hi = __mul64hi(a, b);
     const unsigned long long lo = (unsigned long long)(a * b);
@@ -658,7 +657,9 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
 // (tcgen05.mma issued by one thread, operands in shared memory, accumulators
 // in tensor memory).
 //
-// Digits are balanced here: v = x >> 6 = sum_j X_j 256^(6 - j) with
+// Here the tile holds Q56 (v = x * 2^56, the Q62 value >> 6: the digit
+// split never used the low 6 bits) and digits are balanced:
+// v = sum_j X_j 256^(6 - j) with
 // |X_0| <= 256 and X_j in [-128, 127] for j >= 1 (the bytes of
 // v + 0x808080808080, minus 128), and held as float16, exact for integers
 // below 2^11: one byte permute and one logic op place two bytes b in the
@@ -775,9 +776,9 @@ __device__ __forceinline__ unsigned h2_byte_pair(unsigned w0, unsigned w1) {
     return sub_h2(t, 0x64806480u);                                            // minus 1024 + 128
 }
 
-// The seven balanced digits of two Q62 values, packed pairwise as fp16 x 2.
+// The seven balanced digits of two Q56 values, packed pairwise as fp16 x 2.
 __device__ __forceinline__ void bal_digits_pair(long long x0, long long x1, unsigned (&o)[7]) {
-    const long long u0 = (x0 >> 6) + 0x808080808080ll, u1 = (x1 >> 6) + 0x808080808080ll;
+    const long long u0 = x0 + 0x808080808080ll, u1 = x1 + 0x808080808080ll;
     const unsigned lo0 = (unsigned)u0, hi0 = (unsigned)((unsigned long long)u0 >> 32);
     const unsigned lo1 = (unsigned)u1, hi1 = (unsigned)((unsigned long long)u1 >> 32);
     // top digit d (|d| <= 256): fp16 bits of 1536 + d are 0x6600 + d
@@ -838,6 +839,19 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
     const int e_cg = K == 4 ? warp >> 2 : (warp >> 2) & 1;
     const int e_mt = K == 4 ? 0 : warp >> 3;
     const int e_row = (warp & 3) * 32 + lane;
+    // Offsets fixed for the op: a group index is round base | local index
+    // (disjoint bits), insert_zero_bits maps disjoint bits to disjoint bits
+    // and the swizzle is linear over GF(2), so a slot is
+    // swz(iz(base)) ^ swz(iz(local)) ^ swz(offset of the amplitude).
+    int s_off[4], e_off[4];
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        s_off[e] = swz<double>(group_offset<K>(4 * s_qa + e, pm));
+        e_off[e] = swz<double>(group_offset<K>(4 * e_cg + e, pm));
+    }
+    const int s_loc = s_mt * 128 + s_row, e_loc = e_mt * 128 + e_row;
+    const int s_sw = swz<double>(insert_zero_bits<K>(s_loc, pos));
+    const int e_sw = swz<double>(insert_zero_bits<K>(e_loc, pos));
     // re-assembly of the round starting at group r0 from TMEM buffer tbuf
     auto reassemble = [&](int r0, int r_mt, uint32_t tbuf) {
         fence_after();
@@ -863,20 +877,18 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
         }
         ld8(t0 + 6 * R, a);
         ld_wait();
-        const int G = r0 + e_mt * 128 + e_row;
-        if (G < ng) {
-            const int bg = swz<double>(insert_zero_bits<K>(G, pos));
-            // y = 2^6 (P01 2^32 + P23 2^16 + P45) + Z_6 / 4 (rounded), in Q62 units
+        if (r0 + e_loc < ng) {
+            const int bg = swz<double>(insert_zero_bits<K>(r0, pos)) ^ e_sw;
+            // y = P01 2^32 + P23 2^16 + P45 + Z_6 / 256 (rounded), in Q56 units
             auto out = [&](int e) {
-                const int t6 = (int)(__float_as_uint(__uint_as_float(a[e]) + 12582912.0f) - kMagicBits + 2u) >> 2;
-                return (long long)(((unsigned long long)(long long)P[0][e] << 38) +
-                                   ((unsigned long long)(long long)P[1][e] << 22) +
-                                   ((unsigned long long)(long long)P[2][e] << 6) +
-                                   (unsigned long long)(long long)t6);
+                const int t6 = (int)(__float_as_uint(__uint_as_float(a[e]) + 12582912.0f) - kMagicBits + 128u) >> 8;
+                return (long long)(((unsigned long long)(long long)P[0][e] << 32) +
+                                   ((unsigned long long)(long long)P[1][e] << 16) +
+                                   (unsigned long long)(long long)(P[2][e] + t6));
             };
 #pragma unroll
             for (int e = 0; e < 4; e++)
-                sm[bg ^ swz<double>(group_offset<K>(4 * e_cg + e, pm))] = Q2{out(e), out(e + 4)};
+                sm[bg ^ e_off[e]] = Q2{out(e), out(e + 4)};
         }
     };
     // Rounds are pipelined over two TMEM accumulators: the MMAs of round r
@@ -885,12 +897,11 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
     uint32_t prev_buf = 0;
     for (int g0 = 0; g0 < ng; g0 += GPR) {
         {
-            const int G = g0 + s_mt * 128 + s_row;
-            if (G < ng) {
-                const int bg = swz<double>(insert_zero_bits<K>(G, pos));
+            if (g0 + s_loc < ng) {
+                const int bg = swz<double>(insert_zero_bits<K>(g0, pos)) ^ s_sw;
                 Q2 v[4];
 #pragma unroll
-                for (int e = 0; e < 4; e++) v[e] = sm[bg ^ swz<double>(group_offset<K>(4 * s_qa + e, pm))];
+                for (int e = 0; e < 4; e++) v[e] = sm[bg ^ s_off[e]];
                 // component k = part D + 4 qa + e: k-core k >> 3, byte (k & 7) * 2
                 unsigned char* row0 = cx.a + s_mt * 7 * PLANE + (s_row >> 3) * SBO + (s_row & 7) * 16 + (s_qa & 1) * 8;
                 store_digits4(v[0].re, v[1].re, v[2].re, v[3].re, row0 + (s_qa >> 1) * 128, PLANE);
@@ -1125,12 +1136,23 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
                 sm[swz<double>(j)] = v;
             }
         } else if constexpr (MODE == MODE_TC || MODE == MODE_T05) {
-            const int N = 1 << m;
-            for (int j = threadIdx.x; j < N; j += blockDim.x) {
-                const int r = j >> c;
-                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
-                const Cx<double> a = st[gidx];
-                sm[swz<double>(j)] = Q2{d2q(a.re), d2q(a.im)};
+            // fixed-point tile: Q62 (mma.sync mode), Q56 (tcgen05 mode, whose digits are those of x >> 6)
+            constexpr int kTileFB = MODE == MODE_T05 ? 56 : 62;
+            // loads in flight per thread before the conversions
+            constexpr int U = MODE == MODE_T05 ? 8 : 4;
+            const int N = 1 << m, nt = blockDim.x;
+            for (int j0 = threadIdx.x; j0 < N; j0 += U * nt) {
+                Cx<double> a[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int j = j0 + u * nt, r = j >> c;
+                    if (j < N) a[u] = st[base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)];
+                }
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int j = j0 + u * nt;
+                    if (j < N) sm[swz<double>(j)] = Q2{d2q<kTileFB>(a[u].re), d2q<kTileFB>(a[u].im)};
+                }
             }
         } else {
             constexpr int PER = 16 / sizeof(Store);  // amplitudes per 16-byte vector
@@ -1143,6 +1165,26 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
             }
         }
         __syncthreads();
+        {
+            // Prefetch the CTA's next tile (same entry) into L2 while this one
+            // is computed: one bulk prefetch per run of 2^c contiguous
+            // amplitudes (256 bytes), so the next load phase reads from L2.
+            // (Measured: faster for the FP32 / FP64 / double-float passes,
+            // slower for the fixed-point tensor-core passes.)
+            const uint64_t tn = t + gridDim.x;
+            const int runs = 1 << (m - c);
+            constexpr bool kPrefetch = MODE != MODE_TC && MODE != MODE_T05;
+            if (kPrefetch && tn < total_tiles && tn - s_begin < P.tile_count && (int)threadIdx.x < runs) {
+                const uint64_t tln = tn - s_begin;
+                uint64_t bn = 0;
+                for (int b = 0; b < P.n - m; b++)
+                    if ((tln >> b) & 1) bn |= 1ull << P.NL[b];
+                const int r = threadIdx.x;
+                const Store* src = st + (bn | dep[0][r & 31] | dep[1][(r >> 5) & 31]);
+                asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"((int)(sizeof(Store) << c))
+                             : "memory");
+            }
+        }
         const int n_ops = P.n_ops, op0 = P.op0;
         for (int o = 0; o < n_ops; o++) {
             const DevOp op = n_ops <= kOpCache ? s_ops[o] : ops[op0 + o];
@@ -1169,12 +1211,13 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
                 st[gidx] = Cx<double>{df2d(v.rh, v.rl), df2d(v.ih, v.il)};
             }
         } else if constexpr (MODE == MODE_TC || MODE == MODE_T05) {
+            constexpr int kTileFB = MODE == MODE_T05 ? 56 : 62;
             const int N = 1 << m;
             for (int j = threadIdx.x; j < N; j += blockDim.x) {
                 const int r = j >> c;
                 const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
                 const Q2 v = sm[swz<double>(j)];
-                st[gidx] = Cx<double>{q2d(v.re), q2d(v.im)};
+                st[gidx] = Cx<double>{q2d<kTileFB>(v.re), q2d<kTileFB>(v.im)};
             }
         } else {
             constexpr int PER = 16 / sizeof(Store);
