@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--form", default="full", choices=["full", "batch", "serve"],
                     help="full: one circuit (default); batch: the 91 cut-subcircuit variants of the "
                          "40-qubit brickwork; serve: a Poisson request stream")
+    ap.add_argument("--circuit", default="ghz_brickwork", choices=["ghz_brickwork", "brickwork", "qaoa"],
+                    help="full form: GHZ + brickwork depth --depth seed 2 (default); brickwork depth --depth "
+                         "seed 1 (12 q, depth 10, --fuse 1: the unfused 175-gate circuit); QAOA p = 2 seed 3 "
+                         "on a random 3-regular graph")
     ap.add_argument("--serve-count", type=int, default=2000)
     ap.add_argument("--serve-wmax", type=int, default=30)
     return ap.parse_args()
@@ -135,18 +139,20 @@ def kernel_hash():
 
 
 def ncu_traffic(workload_key, per_launch_scale):
-    """DRAM bytes per tile-pass launch from the committed ncu summary, or None
-    when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    try:
+    """DRAM bytes (read + write) per tile-pass launch from the committed ncu
+    summaries: a line `traffic-record: key=<workload> bytes=<per launch>
+    kernel_hash=<hash>` in profiles/*.md.  None when there is no record or the
+    kernel source changed since the capture."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as f:
-            d = json.load(f)
-    except (OSError, ValueError):
-        return None
-    e = d.get(workload_key)
-    if not e or e.get("kernel_hash") != kernel_hash():
-        return None
-    return e["dram_bytes_per_launch"] * per_launch_scale
+            for line in f:
+                if not line.startswith("traffic-record:"):
+                    continue
+                kv = dict(tok.split("=", 1) for tok in line.split()[1:] if "=" in tok)
+                if kv.get("key") == workload_key and kv.get("kernel_hash") == kernel_hash():
+                    return float(kv["bytes"]) * per_launch_scale
+    return None
 
 
 def cpu_baseline(n, gates, seconds, state_bytes_c128):
@@ -338,7 +344,15 @@ def main():
             dist.barrier()
 
     n, dt = args.n, args.dtype
-    gates = W.workload_ghz_brickwork(n, args.depth, 2)
+    if args.circuit == "qaoa":
+        gates = W.workload_qaoa(n, 2, 3)[0]
+        wl_name = f"{n}q QAOA p=2 seed 3 on a random 3-regular graph ({len(gates)} gates)"
+    elif args.circuit == "brickwork":
+        gates = W.brickwork(n, args.depth, 1)
+        wl_name = f"{n}q brickwork depth {args.depth} seed 1 ({len(gates)} gates)"
+    else:
+        gates = W.workload_ghz_brickwork(n, args.depth, 2)
+        wl_name = f"{n}q GHZ + brickwork depth {args.depth} seed 2 ({len(gates)} gates)"
     ctype = torch.complex128 if dt == "c128" else torch.complex64
     amp_bytes = 16 if dt == "c128" else 8
     state_bytes = (1 << n) * amp_bytes
@@ -435,8 +449,9 @@ def main():
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if dt == "c128" else "f32", "data": "synthetic",
-           "config": {"workload": f"{n}q GHZ + brickwork depth {args.depth} seed 2 ({len(gates)} gates), "
-                                  f"complex{128 if dt == 'c128' else 64}, fusion k<=5 autotuned",
+           "config": {"workload": f"{wl_name}, "
+                                  f"complex{128 if dt == 'c128' else 64}, "
+                                  + (f"fusion k<={args.fuse}" if args.fuse else "fusion k<=5 autotuned"),
                       "n_qubits": n, "state_dtype": dt, "arith": "fp32" if dt == "c64" else {1: "native-fp64", 2: "df64", 3: "tcgen05-digits", 4: "mma-sync-digits"}.get(arith, "df64"),
                       "fuse_k": s0["fuse_k"], "tile_qubits": s0["tile_qubits"], "passes": passes,
                       "blocks": s0["n_blocks"], "l2": f"state {state_bytes >> 30} GiB > L2, no flush needed",
