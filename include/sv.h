@@ -84,9 +84,12 @@ typedef struct {
  *   SV_ARITH_TC_SYNC: the same digit products on the warp-level mma.sync
  *                    path (unsigned lower digits), kept as the measured
  *                    baseline of the tensor-memory kernel.
- *   SV_ARITH_AUTO:   SV_ARITH_TC for states of 8 or more qubits, else
- *                    SV_ARITH_DF64 (on GB300 the FP64 pipe runs at about 1/70
- *                    of the FP32 pipe).  Amplitudes supplied by the caller
+ *   SV_ARITH_AUTO:   SV_ARITH_TC for states of 19 or more qubits, else
+ *                    SV_ARITH_DF64 (measured crossover; on GB300 the FP64
+ *                    pipe runs at about 1/70 of the FP32 pipe, so native
+ *                    FP64 is never the automatic choice).  SV_ARITH_TC and
+ *                    SV_ARITH_TC_SYNC fall back to SV_ARITH_DF64 below 8
+ *                    qubits.  Amplitudes supplied by the caller
  *                    (sv_set_amplitudes, sv_create_on) are checked once:
  *                    if a component exceeds 1 in magnitude the call uses
  *                    SV_ARITH_DF64 instead; so does a block whose digit sums
@@ -107,7 +110,12 @@ typedef enum {
  *   tile_qubits:  qubits per shared-memory tile (cache blocking, the
  *                 single-GPU counterpart of the chunk size nc, Sec. III-B).
  *   arith:        sv_arith for complex128 states.
- *   debug_checks: nonzero = check the plan's invariants before launching.
+ *   debug_checks: bit 0 (1): check the plan's invariants before launching
+ *                 (SV_ERR_STATE if one fails).  bit 1 (2): failure-detection
+ *                 test hook for SV_ARITH_TC: the call's first dense block
+ *                 issues no MMAs, so the kernel's bounded wait (one second)
+ *                 runs out; the call returns SV_ERR_TIMEOUT and leaves the
+ *                 state undefined until sv_reset / sv_set_amplitudes.
  *   timing:       nonzero = record CUDA events around every kernel launch on
  *                 the handle's stream and report the durations in
  *                 sv_apply_stats (kernel_ms, max_kernel_ms).               */

@@ -113,17 +113,21 @@ int max_tile(int dt, const svk::DevInfo& di) {
     return m;
 }
 
-// complex128 defaults to double-float arithmetic (same 1e-12 parity as native
-// float64, about 3x faster on GB300's FP32 pipe); SV_ARITH_NATIVE forces FP64.
-// The tensor-core mode needs tiles of at least 8 qubits (an MMA n-tile spans
-// 8 groups of up to 5 qubits); smaller states use double-float arithmetic.
+// complex128 arithmetic.  SV_ARITH_AUTO takes the tensor-memory digit mode
+// from kAutoTcQubits qubits on (measured crossover on GB300: below it the
+// state is a handful of tiles and the double-float pass, with less work per
+// op, is faster) and double-float arithmetic below; explicit tensor-core
+// modes need tiles of at least 8 qubits and fall back to double-float below.
+constexpr int kAutoTcQubits = 19;
+
 int resolve_arith(int dt, const sv_run_opts* o, int n = 34) {
     if (dt == SV_C64) return SV_ARITH_NATIVE;
-    int a = o ? o->arith : 0;
+    const int a = o ? o->arith : 0;
     if (a == SV_ARITH_NATIVE) return SV_ARITH_NATIVE;
-    if (a == SV_ARITH_DF64) return SV_ARITH_DF64;
-    if (n < 8) return SV_ARITH_DF64;
-    return a == SV_ARITH_TC_SYNC ? SV_ARITH_TC_SYNC : SV_ARITH_TC;  // SV_ARITH_TC and SV_ARITH_AUTO
+    if (a == SV_ARITH_DF64 || n < 8) return SV_ARITH_DF64;
+    if (a == SV_ARITH_TC_SYNC) return SV_ARITH_TC_SYNC;
+    if (a == SV_ARITH_TC) return SV_ARITH_TC;
+    return n >= kAutoTcQubits ? SV_ARITH_TC : SV_ARITH_DF64;
 }
 
 bool is_tc(int arith) { return arith == SV_ARITH_TC || arith == SV_ARITH_TC_SYNC; }
@@ -307,7 +311,9 @@ bool t05_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& 
     return ok;
 }
 
-void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE) {
+// inject_stall (tests only): the first dense tensor-memory block issues no
+// MMAs, so its bounded wait runs out (OPF_TEST_NO_MMA).
+void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE, bool inject_stall = false) {
     L.passes.clear();
     L.ops.clear();
     L.coef.clear();
@@ -373,6 +379,10 @@ void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE) {
                 }
             } else {
                 L.coef.insert(L.coef.end(), b.mat.begin(), b.mat.end());
+            }
+            if (inject_stall && t05 && op.kind == svk::OP_DENSE) {
+                op.flags |= svk::OPF_TEST_NO_MMA;
+                inject_stall = false;
             }
             L.ops.push_back(op);
             if (op.kind == svk::OP_DENSE) dp.kmax = std::max(dp.kmax, (int32_t)op.k);
@@ -442,9 +452,9 @@ size_t coef_bytes(const Lowered& L, int dt) {
 // caller re-plans in double-float arithmetic).
 constexpr int kRetryDF64 = 1;
 
-int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing) {
+int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing, bool inject_stall = false) {
     Lowered L;
-    lower(P, L, arith);
+    lower(P, L, arith, inject_stall);
     if (!L.tc_ok) return kRetryDF64;
     const size_t ops_bytes = L.ops.size() * sizeof(DevOp);
     const size_t coef_off = align256(ops_bytes);
@@ -628,7 +638,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     if (ng == 0) return SV_OK;
     const double t0 = now_ms();
     svp::Plan P = plan_for(s->n, s->dt, g, ng, o, max_tile(s->dt, s->di));
-    if (o && o->debug_checks && svp::check_plan(P, ng, g) != 0) return SV_ERR_STATE;
+    if (o && (o->debug_checks & 1) && svp::check_plan(P, ng, g) != 0) return SV_ERR_STATE;
     const double t1 = now_ms();
     int arith = resolve_arith(s->dt, o, s->n);
     if (is_tc(arith) && s->foreign) {
@@ -648,7 +658,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
         df.arith = SV_ARITH_DF64;
         P = plan_for(s->n, s->dt, g, ng, &df, max_tile(s->dt, s->di));
     }
-    rc = apply_plan(s, P, arith, o && o->timing);
+    rc = apply_plan(s, P, arith, o && o->timing, o && (o->debug_checks & 2));
     if (rc == kRetryDF64) {  // a block outside the digit scheme's exact range
         sv_run_opts df = o ? *o : sv_run_opts{};
         df.arith = SV_ARITH_DF64;

@@ -7,7 +7,9 @@ namespace svk {
 constexpr int kMaxQ = 40;
 
 enum OpKind : int32_t { OP_DENSE = 0, OP_DIAG = 1 };
-enum OpFlags : int32_t { OPF_SIGN_ONLY = 1 };
+// OPF_TEST_NO_MMA (tensor-memory mode, tests only): the op issues no MMAs,
+// so its bounded wait runs out and the call reports SV_ERR_TIMEOUT.
+enum OpFlags : int32_t { OPF_SIGN_ONLY = 1, OPF_TEST_NO_MMA = 2 };
 
 // One fused block inside a tile pass (64 bytes).
 struct alignas(16) DevOp {

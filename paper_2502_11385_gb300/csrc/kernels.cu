@@ -696,7 +696,8 @@ constexpr int kSmemMin = 116 * 1024;       // one CTA per SM (it holds all 512 T
 constexpr int kTmemCols = 512;             // two accumulator buffers
 constexpr uint32_t kTmemBuf = 256;         // column offset of the second buffer
 constexpr unsigned kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
-constexpr int kWaitSpins = 1 << 20;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
+constexpr unsigned kWaitPolls = 1u << 26;                 // and after this many polls in any case
 
 __device__ int g_fault;  // set when a bounded wait ran out (read and cleared by the host)
 
@@ -728,10 +729,18 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
                  : "memory");
 }
 
-// Waits for the phase of the given parity to complete; false after kWaitSpins
-// polls (the caller reports SV_ERR_TIMEOUT instead of hanging).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of the given parity to complete; false after kWaitNs
+// nanoseconds (or kWaitPolls polls), so the caller reports SV_ERR_TIMEOUT
+// instead of hanging.
 __device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
-    for (int it = 0; it < kWaitSpins; it++) {
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < kWaitPolls; it++) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -740,6 +749,7 @@ __device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
     }
     return false;
 }
@@ -913,7 +923,8 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
         __syncthreads();
         const int n_mt = (K == 3 && g0 + 128 < ng) ? 2 : 1;
         const uint32_t buf = (uint32_t)((g0 / GPR) & 1) * kTmemBuf;
-        if (tid == 0) {
+        // (OPF_TEST_NO_MMA, a test hook: nothing is issued, so the bounded wait runs out)
+        if (tid == 0 && !(op.flags & OPF_TEST_NO_MMA)) {
             fence_after();
             for (int mt = 0; mt < n_mt; mt++)
 #pragma unroll

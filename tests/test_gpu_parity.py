@@ -469,7 +469,7 @@ def test_tc_small_states_fall_back(sv):
 def test_auto_arith_falls_back_for_unnormalised_amplitudes(sv):
     """A caller-supplied state with components above 1 in magnitude is outside
     the tensor-core mode's fixed-point range: the call uses double-float."""
-    n = 10
+    n = 20
     rng = np.random.default_rng(4)
     v = 3.0 * (rng.normal(size=1 << n) + 1j * rng.normal(size=1 << n))
     g = _random_circuit(n, 30, 77)
@@ -483,3 +483,36 @@ def test_auto_arith_falls_back_for_unnormalised_amplitudes(sv):
         s.apply_circuit(g)
         assert s.stats()["arith"] == sv.ARITH_TC
         assert np.abs(s.amplitudes() - oracle.apply(n, (v / np.linalg.norm(v)).copy(), g)).max() <= 1e-12
+
+
+def test_auto_arith_threshold(sv):
+    """SV_ARITH_AUTO: double-float below 19 qubits, tcgen05 digits from 19 on."""
+    for n, want in ((18, sv.ARITH_DF64), (19, sv.ARITH_TC)):
+        g = _random_circuit(n, 40, 700 + n)
+        st = _check(sv, n, "c128", g)
+        assert st["arith"] == want, (n, st["arith"])
+
+
+def test_tc_bounded_wait_reports_timeout_and_recovers(sv):
+    """Failure detection without a GPU fault: a test hook makes the first
+    tensor-memory block issue no MMAs, so the kernel's bounded wait (one
+    second) runs out.  The call reports SV_ERR_TIMEOUT, the handle refuses
+    further use until it is reset, and the context stays usable."""
+    import time
+    n = 14
+    g = _random_circuit(n, 60, 1234)
+    ref = oracle.run(n, g)
+    with sv.State(n, "c128") as s:
+        t0 = time.perf_counter()
+        with pytest.raises(sv.SvError) as e1:
+            s.apply_circuit(g, sv.run_opts(arith=sv.ARITH_TC, debug_checks=2))
+        assert e1.value.code == sv.SV_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 30
+        with pytest.raises(sv.SvError) as e2:
+            s.probabilities()
+        assert e2.value.code == sv.SV_ERR_STATE
+        s.reset(0)
+        s.apply_circuit(g, sv.run_opts(arith=sv.ARITH_TC))
+        assert np.abs(s.amplitudes() - ref).max() <= 1e-12
+    # a fresh handle on the same context works as well
+    _check(sv, n, "c128", g, ref, arith=sv.ARITH_TC)
