@@ -452,7 +452,8 @@ def main():
            "config": {"workload": f"{wl_name}, "
                                   f"complex{128 if dt == 'c128' else 64}, "
                                   + (f"fusion k<={args.fuse}" if args.fuse else "fusion k<=5 autotuned"),
-                      "n_qubits": n, "state_dtype": dt, "arith": "fp32" if dt == "c64" else {1: "native-fp64", 2: "df64", 3: "tcgen05-digits", 4: "mma-sync-digits"}.get(arith, "df64"),
+                      "n_qubits": n, "state_dtype": dt, "arith": ({3: "tcgen05-bf16x3"}.get(arith, "fp32") if dt == "c64" else
+                                {1: "native-fp64", 2: "df64", 3: "tcgen05-digits", 4: "mma-sync-digits"}.get(arith, "df64")),
                       "fuse_k": s0["fuse_k"], "tile_qubits": s0["tile_qubits"], "passes": passes,
                       "blocks": s0["n_blocks"], "l2": f"state {state_bytes >> 30} GiB > L2, no flush needed",
                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},

@@ -95,7 +95,11 @@ typedef struct {
  *                    SV_ARITH_DF64 instead; so does a block whose digit sums
  *                    could exceed the exact float32 range (none for unitary
  *                    blocks).
- * complex64 states always compute in float32. */
+ * complex64 states: SV_ARITH_NATIVE (and SV_ARITH_DF64 / SV_ARITH_TC_SYNC)
+ * compute in float32 FMAs; SV_ARITH_TC splits every float32 component into
+ * three bfloat16 parts and forms the six part products of float32 accuracy
+ * on the tensor cores (tcgen05.mma, float32 accumulation in tensor memory);
+ * SV_ARITH_AUTO takes SV_ARITH_TC from 19 qubits on.  No magnitude limit. */
 typedef enum {
     SV_ARITH_AUTO = 0,
     SV_ARITH_NATIVE = 1,
@@ -242,7 +246,9 @@ int sv_last_stats(const sv_state* s, sv_apply_stats* out);
  * own (its result does not depend on the other items), and pass i of every
  * item runs in one multi-state tile-pass launch.  The whole sequence (init,
  * passes, probabilities) is captured once in a CUDA graph that
- * sv_batch_execute replays.  item_status[i] receives each item's sv_status
+ * sv_batch_execute replays, on a stream of the highest priority (its
+ * launches are scheduled ahead of pending launches on other streams; running
+ * kernels are not preempted).  item_status[i] receives each item's sv_status
  * (may be NULL); invalid items are skipped, the others still run. */
 typedef struct {
     int32_t n_qubits;

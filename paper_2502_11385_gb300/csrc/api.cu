@@ -103,7 +103,7 @@ cudaError_t device_info(svk::DevInfo* out) {
 // always in the tile (runs of 2^c contiguous amplitudes = 256 bytes).  The
 // tensor-memory mode takes 128 KiB tiles (one CTA per SM, 16 warps).
 int default_tile(int dt, int arith = SV_ARITH_NATIVE) {
-    if (dt == SV_C64) return 13;
+    if (dt == SV_C64) return arith == SV_ARITH_TC ? 14 : 13;
     return arith == SV_ARITH_TC ? 13 : 12;
 }
 int coalesce_of(int dt) { return dt == SV_C64 ? 5 : 4; }
@@ -121,8 +121,11 @@ int max_tile(int dt, const svk::DevInfo& di) {
 constexpr int kAutoTcQubits = 19;
 
 int resolve_arith(int dt, const sv_run_opts* o, int n = 34) {
-    if (dt == SV_C64) return SV_ARITH_NATIVE;
     const int a = o ? o->arith : 0;
+    if (dt == SV_C64) {  // float32 FMAs, or the bfloat16 triple split on the tensor cores
+        if (n < 8 || (a != SV_ARITH_TC && a != SV_ARITH_AUTO)) return SV_ARITH_NATIVE;
+        return (a == SV_ARITH_TC || n >= kAutoTcQubits) ? SV_ARITH_TC : SV_ARITH_NATIVE;
+    }
     if (a == SV_ARITH_NATIVE) return SV_ARITH_NATIVE;
     if (a == SV_ARITH_DF64 || n < 8) return SV_ARITH_DF64;
     if (a == SV_ARITH_TC_SYNC) return SV_ARITH_TC_SYNC;
@@ -137,13 +140,13 @@ svp::Plan plan_for(int n, int dt, const sv_gate* g, size_t ng, const sv_run_opts
     if (k < 0) k = 0;
     if (k > svp::kMaxFuse) k = svp::kMaxFuse;
     const int c = coalesce_of(dt);
-    const int arith = dt == SV_C128 ? resolve_arith(dt, o, n) : SV_ARITH_NATIVE;
+    const int arith = resolve_arith(dt, o, n);
     int m = (o && o->tile_qubits > 0) ? o->tile_qubits : default_tile(dt, arith);
     m = std::min(m, smem_max_m);
     m = std::min(m, c + 10);
     m = std::max(m, c + svp::kMaxFuse);
     svp::Machine mc;
-    int ak = svp::AK_FP32;
+    int ak = arith == SV_ARITH_TC ? svp::AK_TC32 : svp::AK_FP32;
     if (dt == SV_C128) ak = arith == SV_ARITH_DF64 ? svp::AK_DF64 : (is_tc(arith) ? svp::AK_TC : svp::AK_FP64);
     return svp::make_plan(n, g, ng, k, m, c, amp_bytes(dt), ak, mc);
 }
@@ -313,16 +316,65 @@ bool t05_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& 
 
 // inject_stall (tests only): the first dense tensor-memory block issues no
 // MMAs, so its bounded wait runs out (OPF_TEST_NO_MMA).
-void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE, bool inject_stall = false) {
+// Block parts for the complex64 tensor-core kernel: B is 3R x R bf16, row
+// j R + r' = part j of real-form row r (x = h + m + l, h = bf16(x),
+// m = bf16(x - h), l = bf16(x - h - m), from the float64 entry), with
+// r' = (amp / P) 2P + part P + (amp mod P), P = D / 4; column c = real-form
+// column; K-major core matrices of 8 rows x 16 bytes (128 bytes between core
+// matrices along K, 16 R bytes along N).
+uint16_t bf16_rn(double x) {
+    float f = (float)x;  // float64 -> float32 -> bfloat16, both to nearest (the parts below
+    uint32_t u;          // absorb the double rounding: x - h is formed from x itself)
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+double bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return (double)f;
+}
+void t32_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& out) {
+    const int D = 1 << k, R = 2 * D, SBO = 16 * R, Pq = D / 4;
+    std::vector<uint16_t> img((size_t)3 * R * R, 0);
+    for (int r = 0; r < R; r++) {
+        const int part = r / D, amp = r % D;
+        const int rp = (amp / Pq) * 2 * Pq + part * Pq + (amp % Pq);
+        for (int c = 0; c < R; c++) {
+            const svp::cd u = M[(size_t)amp * D + (c % D)];
+            double v;
+            if (part == 0) v = c < D ? u.real() : -u.imag();
+            else v = c < D ? u.imag() : u.real();
+            const uint16_t h = bf16_rn(v);
+            const double r1 = v - bf16_value(h);
+            const uint16_t m = bf16_rn(r1);
+            const uint16_t l = bf16_rn(r1 - bf16_value(m));
+            const uint16_t parts[3] = {h, m, l};
+            for (int j = 0; j < 3; j++) {
+                const int n = j * R + rp;
+                img[((size_t)(n >> 3) * SBO + (size_t)(c >> 3) * 128 + (n & 7) * 16 + (c & 7) * 2) / 2] = parts[j];
+            }
+        }
+    }
+    const size_t at = out.size();
+    out.resize(at + img.size() * 2 / sizeof(Word16));
+    std::memcpy(out.data() + at, img.data(), img.size() * 2);
+}
+
+void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE, bool inject_stall = false,
+           int dt = SV_C128) {
     L.passes.clear();
     L.ops.clear();
     L.coef.clear();
     L.tc.clear();
     L.is_tc = is_tc(arith);
     L.tc_ok = true;
-    const bool t05 = arith == SV_ARITH_TC;
+    const bool t05 = arith == SV_ARITH_TC;  // tcgen05 (complex128 digits or complex64 triple split)
+    const bool c64 = dt == SV_C64;
     auto block_digits = [&](int k, const std::vector<svp::cd>& M) {
-        if (t05) L.tc_ok = t05_block_image(k, M, L.tc) && L.tc_ok;
+        if (c64) t32_block_image(k, M, L.tc);
+        else if (t05) L.tc_ok = t05_block_image(k, M, L.tc) && L.tc_ok;
         else tc_fragments(k, M, L.tc);
     };
     for (const auto& ps : P.passes) {
@@ -358,7 +410,18 @@ void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE, bool inj
             }
             if (L.is_tc) {
                 op.coeff = (int32_t)L.tc.size();
-                if (op.kind == svk::OP_DIAG) {
+                if (op.kind == svk::OP_DIAG && c64) {  // float pairs, two entries per 16 bytes
+                    for (size_t e = 0; e < b.mat.size(); e += 2) {
+                        float f[4] = {(float)b.mat[e].real(), (float)b.mat[e].imag(), 0.f, 0.f};
+                        if (e + 1 < b.mat.size()) {
+                            f[2] = (float)b.mat[e + 1].real();
+                            f[3] = (float)b.mat[e + 1].imag();
+                        }
+                        Word16 w;
+                        std::memcpy(&w, f, 16);
+                        L.tc.push_back(w);
+                    }
+                } else if (op.kind == svk::OP_DIAG) {
                     for (const auto& u : b.mat) {
                         const int64_t re = q62_of(u.real()), im = q62_of(u.imag());
                         Word16 w;
@@ -454,7 +517,7 @@ constexpr int kRetryDF64 = 1;
 
 int apply_plan(sv_state* s, const svp::Plan& P, int arith, bool timing, bool inject_stall = false) {
     Lowered L;
-    lower(P, L, arith, inject_stall);
+    lower(P, L, arith, inject_stall, s->dt);
     if (!L.tc_ok) return kRetryDF64;
     const size_t ops_bytes = L.ops.size() * sizeof(DevOp);
     const size_t coef_off = align256(ops_bytes);
@@ -641,7 +704,7 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     if (o && (o->debug_checks & 1) && svp::check_plan(P, ng, g) != 0) return SV_ERR_STATE;
     const double t1 = now_ms();
     int arith = resolve_arith(s->dt, o, s->n);
-    if (is_tc(arith) && s->foreign) {
+    if (s->dt == SV_C128 && is_tc(arith) && s->foreign) {
         // caller-supplied amplitudes: the fixed-point tile needs |re|, |im| <= 1
         SV_TRY(ensure(&s->d_red, &s->d_red_cap, 256, false));
         SV_TRY(svk::launch_max_abs_c128(s->amp, s->n, (unsigned long long*)s->d_red, s->stream, s->di));
@@ -831,13 +894,13 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         bp.dt = it.dt;
         bp.arith = resolve_arith(it.dt, opts, it.n_qubits);
         bp.plan = plan_for(it.n_qubits, it.dt, it.gates, it.n_gates, opts, max_tile(it.dt, b->di));
-        lower(bp.plan, bp.low, bp.arith);
+        lower(bp.plan, bp.low, bp.arith, false, bp.dt);
         if (!bp.low.tc_ok) {  // a block outside the digit scheme's exact range: double-float
             sv_run_opts df = opts ? *opts : sv_run_opts{};
             df.arith = SV_ARITH_DF64;
             bp.arith = SV_ARITH_DF64;
             bp.plan = plan_for(it.n_qubits, it.dt, it.gates, it.n_gates, &df, max_tile(it.dt, b->di));
-            lower(bp.plan, bp.low, bp.arith);
+            lower(bp.plan, bp.low, bp.arith, false, bp.dt);
         }
         bp.host_out = !it.probs_on_device;
         P.push_back(std::move(bp));
@@ -855,9 +918,9 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         off += align256(((size_t)8) << bp.n);
     }
     // group by kernel mode (dtype, arithmetic): kBatchModes values of mode_of
-    constexpr int kBatchModes = 5;
+    constexpr int kBatchModes = 6;
     auto mode_of = [](const BatchItemPlan& bp) {
-        if (bp.dt == SV_C64) return 0;
+        if (bp.dt == SV_C64) return bp.arith == SV_ARITH_TC ? 5 : 0;
         if (bp.arith == SV_ARITH_DF64) return 2;
         if (bp.arith == SV_ARITH_TC) return 3;
         return bp.arith == SV_ARITH_TC_SYNC ? 4 : 1;
@@ -885,7 +948,7 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         op_base[i] = ops.size();
         for (auto op : bp.low.ops) ops.push_back(op);
         // coefficient offsets are in elements; keep each item's blob aligned to its element size
-        const size_t esz = coef_elem_bytes(bp.dt);
+        const size_t esz = bp.low.is_tc ? sizeof(Word16) : coef_elem_bytes(bp.dt);  // unit of op.coeff
         size_t cb = (coefs.size() + esz - 1) / esz * esz;
         coefs.resize(cb + coef_bytes(bp.low, bp.dt));
         if (bp.low.is_tc) {
@@ -939,7 +1002,7 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
     }
     // rebase each op's coefficient offset: element offset inside its item's blob
     for (size_t i = 0; i < P.size(); i++) {
-        const size_t esz = coef_elem_bytes(P[i].dt);
+        const size_t esz = P[i].low.is_tc ? sizeof(Word16) : coef_elem_bytes(P[i].dt);
         for (size_t o = 0; o < P[i].low.ops.size(); o++) ops[op_base[i] + o].coeff += (int32_t)(coef_base[i] / esz);
     }
     const size_t ent_off = off;
@@ -989,7 +1052,12 @@ static int batch_build(const sv_batch_item* items, size_t n_items, const sv_run_
         cudaMemcpy(A + sent_off, sentries.data(), sentries.size() * sizeof(svk::StateEntry), cudaMemcpyHostToDevice) !=
             cudaSuccess)
         return fail(SV_ERR_CUDA);
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(SV_ERR_CUDA);
+    // highest stream priority: a batch of small circuits is scheduled ahead of
+    // pending launches of long single-circuit passes on other streams
+    int prio_lo = 0, prio_hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&b->stream, cudaStreamNonBlocking, prio_hi) != cudaSuccess)
+        return fail(SV_ERR_CUDA);
     if (cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess)
         return fail(SV_ERR_CUDA);
     // capture: init (per mode) -> passes -> probabilities (per mode)

@@ -14,6 +14,8 @@
 // Amplitudes are interleaved complex; index bit q is qubit q.
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -220,17 +222,17 @@ __device__ __forceinline__ void diag_at(const DiagIndex& d, int it, int& idx, in
     sidx = d.sw_t ^ swz<SwzT>(it << LT);
 }
 
-template <typename R>
+template <typename R, int LT = 8>  // LT = log2 of the CTA size
 __device__ __forceinline__ void op_diag(Cx<R>* sm, int m, const DevOp& op, const Cx<R>* __restrict__ M,
                                         uint64_t tile_base) {
-    const DiagIndex d = diag_index<R>(op, tile_base);
+    const DiagIndex d = diag_index<R, LT>(op, tile_base);
     const int N = 1 << m;
-    const int iters = (N + 255) >> 8;  // tiles smaller than the CTA: threads past N idle
+    const int iters = (N + (1 << LT) - 1) >> LT;  // tiles smaller than the CTA: threads past N idle
     const bool sign_only = op.flags & OPF_SIGN_ONLY;
     for (int it = 0; it < iters; it++) {
-        if ((int)threadIdx.x + (it << 8) >= N) break;
+        if ((int)threadIdx.x + (it << LT) >= N) break;
         int idx, si;
-        diag_at<R>(d, it, idx, si);
+        diag_at<R, LT>(d, it, idx, si);
         const Cx<R> u = M[idx];
         const Cx<R> a = sm[si];
         if (sign_only) {
@@ -960,9 +962,214 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
 }  // namespace t05
 
 // ---------------------------------------------------------------------------
+// K5-t32: complex64 block products on tcgen05 (bfloat16 triple split).
+//
+// Each float32 component x of the tile is split into three bfloat16 parts,
+// x = h + m + l with h = bf16(x), m = bf16(x - h), l = bf16(x - h - m) (each
+// residual is exact in float32; |x - h - m - l| <= 2^-24 |x|); the block's
+// real form likewise, from its float64 entries.  The six products of parts
+// (i, j) with i + j <= 2 carry float32 accuracy (the dropped ones are below
+// 2^-24 relative): amplitude part i meets block parts 0..2-i in one MMA of
+// N = (3 - i) R into TMEM columns [i R, 3R), so level L = i + j collects in
+// columns [L R, (L+1) R) with float32 accumulation; the output is
+// (Z_2 + Z_1) + Z_0.  No exact re-assembly is needed: complex64 only asks
+// for float32 rounding.
+//
+// One round covers 128 groups (one M = 128 tile) for blocks of 3..5 qubits
+// (smaller blocks are padded to 3): A_i (shared, 128 x R bf16, K-major core
+// matrices of 8 rows x 16 bytes), B (shared, 3R x R bf16, row j R + r' =
+// part j of real-form row r, r' = (amp / P) 2P + part P + (amp mod P) with
+// P = D / 4 amplitudes per thread), D (TMEM, 3R columns).  Rounds are
+// pipelined over two accumulator buffers as in the complex128 mode.
+// ---------------------------------------------------------------------------
+namespace t32 {
+
+constexpr int kABytes = 3 * 128 * 64 * 2;     // 3 part planes of 128 x 64 bf16 (5-qubit blocks)
+constexpr int kBBytes = 6 * 64 * 64;          // 3R x R bf16 for R = 64
+constexpr int kSmemBase = kABytes + kBBytes;  // 72 KiB; the amplitude tile follows
+
+__device__ __forceinline__ uint32_t idesc(int n) {  // kind::f16, f32 accumulator, bf16 A and B, M = 128
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned bf16x2_rn(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&v);
+}
+
+// Three bfloat16 parts of two float32 values, packed pairwise (x0 low half).
+__device__ __forceinline__ void bf3_pair(float x0, float x1, unsigned& h, unsigned& m, unsigned& l) {
+    h = bf16x2_rn(x0, x1);
+    const float r0 = x0 - __uint_as_float(h << 16), r1 = x1 - __uint_as_float(h & 0xFFFF0000u);
+    m = bf16x2_rn(r0, r1);
+    l = bf16x2_rn(r0 - __uint_as_float(m << 16), r1 - __uint_as_float(m & 0xFFFF0000u));
+}
+
+template <int N>
+__device__ __forceinline__ void ldN(uint32_t taddr, uint32_t (&r)[N]);
+template <>
+__device__ __forceinline__ void ldN<4>(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
+template <>
+__device__ __forceinline__ void ldN<8>(uint32_t taddr, uint32_t (&r)[8]) {
+    t05::ld8(taddr, r);
+}
+template <>
+__device__ __forceinline__ void ldN<16>(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Dense block of 3..5 qubits on tcgen05 (bfloat16 triple split).
+// Bg: the block's parts in their shared-memory image (6 R^2 bytes).
+template <int K>
+__device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, const uint4* __restrict__ Bg,
+                                         t05::Ctx& cx) {
+    static_assert(K >= 3 && K <= 5, "tensor-core blocks have 3 to 5 qubits");
+    using namespace t05;
+    constexpr int D = 1 << K, R = 2 * D;
+    constexpr int SBO = 16 * R;         // bytes between 8-row core groups
+    constexpr int PLANE = 128 * R * 2;  // one part plane
+    constexpr int P = D / 4;            // amplitudes per thread
+    int pos[K], pm[K];
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+        pos[j] = op.pos[j];
+        pm[j] = 1 << pos[j];
+    }
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int i = tid; i < 6 * R * R / 16; i += kThreads) cp_async16(cx.b_addr + 16 * i, Bg + i);
+    const int ng = 1 << (m - K);
+    // split: thread -> (row, amplitude group qa of P amplitudes); the lanes of a
+    // warp fill whole core-matrix rows with their stores
+    int s_row, s_qa;
+    if (K == 5) {
+        s_row = tid & 127;
+        s_qa = tid >> 7;
+    } else if (K == 4) {
+        s_row = ((tid >> 5) & 7) * 16 + (lane >> 1);
+        s_qa = 2 * (tid >> 8) + (lane & 1);
+    } else {
+        s_row = tid >> 2;
+        s_qa = tid & 3;
+    }
+    // re-assembly: warp -> (TMEM lane quarter, column group of 2P = P amplitudes)
+    const int e_cg = warp >> 2;
+    const int e_row = (warp & 3) * 32 + lane;
+    int s_off[P], e_off[P];
+#pragma unroll
+    for (int e = 0; e < P; e++) {
+        s_off[e] = swz<float>(group_offset<K>(P * s_qa + e, pm));
+        e_off[e] = swz<float>(group_offset<K>(P * e_cg + e, pm));
+    }
+    const int s_sw = swz<float>(insert_zero_bits<K>(s_row, pos));
+    const int e_sw = swz<float>(insert_zero_bits<K>(e_row, pos));
+    // component k = part D + P qa + e: k-core k >> 3, byte (k & 7) * 2
+    unsigned char* const a_row = cx.a + (s_row >> 3) * SBO + (s_row & 7) * 16;
+    const int k_re = P * s_qa, k_im = D + P * s_qa;
+    unsigned char* const a_re = a_row + (k_re >> 3) * 128 + (k_re & 7) * 2;
+    unsigned char* const a_im = a_row + (k_im >> 3) * 128 + (k_im & 7) * 2;
+    auto split = [&](int g0) {
+        if (g0 + s_row >= ng) return;
+        const int bg = swz<float>(insert_zero_bits<K>(g0, pos)) ^ s_sw;
+        Cx<float> v[P];
+#pragma unroll
+        for (int e = 0; e < P; e++) v[e] = sm[bg ^ s_off[e]];
+        unsigned h[2][P / 2], mm[2][P / 2], l[2][P / 2];
+#pragma unroll
+        for (int e = 0; e < P / 2; e++) {
+            bf3_pair(v[2 * e].re, v[2 * e + 1].re, h[0][e], mm[0][e], l[0][e]);
+            bf3_pair(v[2 * e].im, v[2 * e + 1].im, h[1][e], mm[1][e], l[1][e]);
+        }
+#pragma unroll
+        for (int part = 0; part < 2; part++) {
+            unsigned char* p = part ? a_im : a_re;
+            if constexpr (P == 8) {
+                *reinterpret_cast<uint4*>(p) = make_uint4(h[part][0], h[part][1], h[part][2], h[part][3]);
+                *reinterpret_cast<uint4*>(p + PLANE) = make_uint4(mm[part][0], mm[part][1], mm[part][2], mm[part][3]);
+                *reinterpret_cast<uint4*>(p + 2 * PLANE) = make_uint4(l[part][0], l[part][1], l[part][2], l[part][3]);
+            } else if constexpr (P == 4) {
+                *reinterpret_cast<uint2*>(p) = make_uint2(h[part][0], h[part][1]);
+                *reinterpret_cast<uint2*>(p + PLANE) = make_uint2(mm[part][0], mm[part][1]);
+                *reinterpret_cast<uint2*>(p + 2 * PLANE) = make_uint2(l[part][0], l[part][1]);
+            } else {
+                *reinterpret_cast<unsigned*>(p) = h[part][0];
+                *reinterpret_cast<unsigned*>(p + PLANE) = mm[part][0];
+                *reinterpret_cast<unsigned*>(p + 2 * PLANE) = l[part][0];
+            }
+        }
+    };
+    auto reassemble = [&](int r0, uint32_t tbuf) {
+        fence_after();
+        const uint32_t t0 = cx.tmem + tbuf + ((uint32_t)((warp & 3) * 32) << 16) + 2 * P * e_cg;
+        uint32_t z0[2 * P], z1[2 * P], z2[2 * P];
+        ldN<2 * P>(t0, z0);
+        ldN<2 * P>(t0 + R, z1);
+        ldN<2 * P>(t0 + 2 * R, z2);
+        ld_wait();
+        if (r0 + e_row < ng) {
+            const int bg = swz<float>(insert_zero_bits<K>(r0, pos)) ^ e_sw;
+            auto y = [&](int c) {
+                return (__uint_as_float(z2[c]) + __uint_as_float(z1[c])) + __uint_as_float(z0[c]);
+            };
+#pragma unroll
+            for (int e = 0; e < P; e++) sm[bg ^ e_off[e]] = Cx<float>{y(e), y(P + e)};
+        }
+    };
+    auto issue = [&](int g0) {
+        if (tid != 0 || (op.flags & OPF_TEST_NO_MMA)) return;
+        fence_after();
+        const uint32_t buf = (uint32_t)((g0 >> 7) & 1) * kTmemBuf;
+#pragma unroll
+        for (int i = 0; i < 3; i++)
+#pragma unroll
+            for (int ks = 0; ks < R / 16; ks++) {
+                const uint64_t da = desc(cx.a_addr + i * PLANE + ks * 256, 128, SBO);
+                const uint64_t db = desc(cx.b_addr + ks * 256, 128, SBO);
+                mma(cx.tmem + buf + i * R, da, db, idesc((3 - i) * R), (i | ks) != 0);
+            }
+        commit(cx.mbar);
+    };
+    // the MMAs of round r run while the threads re-assemble round r - 1
+    int g0 = 0;
+    for (;; g0 += 128) {
+        split(g0);
+        cp_async_wait_all();
+        fence_async_smem();
+        __syncthreads();
+        issue(g0);
+        if (g0 > 0) reassemble(g0 - 128, (uint32_t)(((g0 - 128) >> 7) & 1) * kTmemBuf);
+        const bool ok = wait(cx.mbar, cx.phase);
+        cx.phase ^= 1;
+        fence_before();
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(&g_fault, 1);
+            wait(cx.mbar, cx.phase ^ 1);  // give the MMAs in flight one more bounded wait
+            cx.failed = true;
+            return;
+        }
+        if (g0 + 128 >= ng) break;
+    }
+    reassemble(g0, (uint32_t)((g0 >> 7) & 1) * kTmemBuf);
+    fence_before();
+    __syncthreads();
+}
+
+}  // namespace t32
+
+// ---------------------------------------------------------------------------
 // K5: the tile-pass kernel, shared by the arithmetic modes.
 // ---------------------------------------------------------------------------
-enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2, MODE_TC = 3, MODE_T05 = 4 };
+enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2, MODE_TC = 3, MODE_T05 = 4, MODE_T32 = 5 };
+__host__ __device__ constexpr bool uses_tmem(int mode) { return mode == MODE_T05 || mode == MODE_T32; }
 
 template <int MODE>
 struct TileTraits;
@@ -1000,6 +1207,13 @@ struct TileTraits<MODE_T05> {
     using Smem = Q2;
     using Coef = uint4;  // dense: block digits in their shared-memory image; diagonal: Q2 entries
     using SwzT = double;
+};
+template <>
+struct TileTraits<MODE_T32> {
+    using Store = Cx<float>;
+    using Smem = Cx<float>;
+    using Coef = uint4;  // dense: block parts in their shared-memory image; diagonal: Cx<float> entries
+    using SwzT = float;
 };
 
 template <int MODE, int KMAX>
@@ -1050,7 +1264,7 @@ __device__ __forceinline__ void apply_op(typename TileTraits<MODE>::Smem* sm, in
 // apply the pass's ops in order, scatter the tile back.  Persistent: each CTA
 // strides over the flattened tile space of all entries.
 template <int MODE, int KMAX>
-__global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThreads,
+__global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads,
                                   MODE == MODE_TC ? 2 : 1)
     k_tile_pass(const BatchEntry* __restrict__ E, int n_entries, uint64_t total_tiles, const DevOp* __restrict__ ops,
                 const typename TileTraits<MODE>::Coef* __restrict__ coef) {
@@ -1059,8 +1273,9 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
     using Smem = typename Tr::Smem;
     using SwzT = typename Tr::SwzT;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    // tcgen05 mode: digit planes and block digits first, the tile after them
-    Smem* sm = reinterpret_cast<Smem*>(smraw + (MODE == MODE_T05 ? t05::kSmemBase : 0));
+    // tcgen05 modes: digit / part planes and block digits first, the tile after them
+    Smem* sm = reinterpret_cast<Smem*>(
+        smraw + (MODE == MODE_T05 ? t05::kSmemBase : (MODE == MODE_T32 ? t32::kSmemBase : 0)));
     __shared__ uint64_t dep[2][32];  // deposit tables for the tile's high local bits
     __shared__ __align__(16) DevPass P;
     __shared__ uint64_t s_state, s_begin;
@@ -1069,7 +1284,7 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
     constexpr int kOpCache = 48;  // the pass's op descriptors, read once per pass
     __shared__ DevOp s_ops[kOpCache];
     t05::Ctx cx{};
-    if constexpr (MODE == MODE_T05) {
+    if constexpr (uses_tmem(MODE)) {
         if (threadIdx.x < 32) {  // warp 0 owns the tensor-memory allocation
             asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                              t05::smem_addr(&t05_tmem)),
@@ -1085,7 +1300,7 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
         __syncthreads();
         t05::fence_after();
         cx.a = smraw;
-        cx.b = smraw + t05::kABytes;
+        cx.b = smraw + (MODE == MODE_T05 ? t05::kABytes : t32::kABytes);
         cx.a_addr = t05::smem_addr(cx.a);
         cx.b_addr = t05::smem_addr(cx.b);
         cx.mbar = t05::smem_addr(&t05_mbar);
@@ -1184,7 +1399,7 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
             // slower for the fixed-point tensor-core passes.)
             const uint64_t tn = t + gridDim.x;
             const int runs = 1 << (m - c);
-            constexpr bool kPrefetch = MODE != MODE_TC && MODE != MODE_T05;
+            constexpr bool kPrefetch = MODE == MODE_F32 || MODE == MODE_F64 || MODE == MODE_DF;
             if (kPrefetch && tn < total_tiles && tn - s_begin < P.tile_count && (int)threadIdx.x < runs) {
                 const uint64_t tln = tn - s_begin;
                 uint64_t bn = 0;
@@ -1205,12 +1420,20 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
                 else if (op.k <= 3) t05::op_dense<3>(sm, m, op, coef + op.coeff, cx);
                 else t05::op_dense<(KMAX >= 4 ? 4 : 3)>(sm, m, op, coef + op.coeff, cx);  // capped at 4 qubits
                 if (cx.failed) break;  // uniform: decided by a block-wide vote
+            } else if constexpr (MODE == MODE_T32) {
+                if (op.kind == OP_DIAG)
+                    op_diag<float, t05::kLogThreads>(sm, m, op, reinterpret_cast<const Cx<float>*>(coef + op.coeff),
+                                                     base);
+                else if (op.k <= 3) t32::op_dense<3>(sm, m, op, coef + op.coeff, cx);  // smaller blocks are padded
+                else if (op.k == 4) t32::op_dense<(KMAX >= 4 ? 4 : 3)>(sm, m, op, coef + op.coeff, cx);
+                else t32::op_dense<(KMAX >= 5 ? 5 : 3)>(sm, m, op, coef + op.coeff, cx);
+                if (cx.failed) break;
             } else {
                 apply_op<MODE, KMAX>(sm, m, op, coef + op.coeff, base);
             }
             __syncthreads();
         }
-        if constexpr (MODE == MODE_T05) {
+        if constexpr (uses_tmem(MODE)) {
             if (cx.failed) break;  // the state is left undefined; the host reports SV_ERR_TIMEOUT
         }
         if constexpr (MODE == MODE_DF) {
@@ -1242,7 +1465,7 @@ __global__ void __launch_bounds__(MODE == MODE_T05 ? t05::kThreads : kTileThread
         }
         __syncthreads();
     }
-    if constexpr (MODE == MODE_T05) {
+    if constexpr (uses_tmem(MODE)) {
         t05::fence_before();
         __syncthreads();
         if (threadIdx.x < 32) {
@@ -1462,6 +1685,7 @@ static cudaError_t tile_pass_impl(const BatchEntry* d_entries, int n_entries, ui
     using Tr = TileTraits<MODE>;
     size_t smem = ((size_t)1 << max_m) * sizeof(typename Tr::Smem);
     if (MODE == MODE_T05) smem = std::max<size_t>(smem + t05::kSmemBase, t05::kSmemMin);
+    if (MODE == MODE_T32) smem = std::max<size_t>(smem + t32::kSmemBase, t05::kSmemMin);
     static int configured_dev = -1;
     static size_t dyn_max = 0;
     if (configured_dev != di.device) {
@@ -1474,7 +1698,7 @@ static cudaError_t tile_pass_impl(const BatchEntry* d_entries, int n_entries, ui
         configured_dev = di.device;
     }
     if (smem > dyn_max) return cudaErrorInvalidValue;
-    const int threads = MODE == MODE_T05 ? t05::kThreads : kTileThreads;
+    const int threads = uses_tmem(MODE) ? t05::kThreads : kTileThreads;
     int per_sm = 1;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<MODE, KMAX>, threads, smem);
     if (e != cudaSuccess) return e;
@@ -1503,6 +1727,8 @@ cudaError_t launch_tile_pass(int dt, int arith, const BatchEntry* d_entries, int
                              int max_m, int kmax, const DevOp* d_ops, const void* d_coef, cudaStream_t s,
                              const DevInfo& di) {
     if (n_entries <= 0 || total_tiles == 0) return cudaSuccess;
+    if (dt == SV_C64 && arith == SV_ARITH_TC)
+        return tile_pass_mode<MODE_T32>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
     if (dt == SV_C64)
         return tile_pass_mode<MODE_F32>(kmax, d_entries, n_entries, total_tiles, max_m, d_ops, d_coef, s, di);
     if (arith == SV_ARITH_DF64)

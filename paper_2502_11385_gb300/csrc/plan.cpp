@@ -237,15 +237,19 @@ static double block_instr(const Block& b, int arith) {
     return (arith == AK_DF64 ? 44.0 : 4.0) * D;
 }
 
-// Tensor-core mode: bfloat16 MMA flops per amplitude of a dense block (43
-// digit pairs of a real 2D x 2D product, blocks of fewer than 3 qubits padded
-// to 3) and CUDA-core operations per amplitude (digit split, re-assembly).
-static double tc_mma_flops(const Block& b) {
+// Tensor-core modes: 16-bit MMA flops per amplitude of a dense block (digit
+// pairs of a real 2D x 2D product: 28 for complex128, 6 for the complex64
+// triple split; blocks of fewer than 3 qubits padded to 3) and CUDA-core
+// operations per amplitude (digit split, re-assembly).
+static double tc_mma_flops(const Block& b, int arith) {
     if (b.kind == BK_DIAG) return 0.0;
     const int k = std::max(3, b.k);
-    return 28.0 * 8.0 * (double)(1 << k);  // 28 digit pairs of a real 2^(k+1) square product
+    return (arith == AK_TC32 ? 6.0 : 28.0) * 8.0 * (double)(1 << k);
 }
-static double tc_alu(const Block& b) { return b.kind == BK_DIAG ? (b.sign_only ? 2.0 : 40.0) : 150.0; }
+static double tc_alu(const Block& b, int arith) {
+    if (b.kind == BK_DIAG) return b.sign_only ? 2.0 : (arith == AK_TC32 ? 4.0 : 40.0);
+    return arith == AK_TC32 ? 30.0 : 150.0;
+}
 
 double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops, double* alu_ops,
                   double* mma_flops) {
@@ -257,9 +261,9 @@ double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, do
         double fl = 0, instr = 0, smem = 0, mma = 0;
         for (int bi : ps.blocks) {
             fl += block_flops(p.blocks[bi], dim);
-            if (arith == AK_TC) {
-                instr += tc_alu(p.blocks[bi]) * dim;
-                mma += tc_mma_flops(p.blocks[bi]) * dim;
+            if (arith == AK_TC || arith == AK_TC32) {
+                instr += tc_alu(p.blocks[bi], arith) * dim;
+                mma += tc_mma_flops(p.blocks[bi], arith) * dim;
             } else {
                 instr += block_instr(p.blocks[bi], arith) * dim;
             }
@@ -269,7 +273,7 @@ double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, do
         fl_all += fl;
         ops_all += instr;
         mma_all += mma;
-        const double alu = instr / rate + mma / mc.mma_flops;
+        const double alu = instr / rate + mma / (arith == AK_TC32 ? mc.tc05_flops : mc.mma_flops);
         const double hbm = 2.0 * state / mc.hbm_Bps;
         const double sm = smem / mc.smem_Bps;
         total += std::max(std::max(alu, hbm), sm) + mc.launch_s;

@@ -61,7 +61,9 @@ struct Plan {
 
 // Arithmetic of the tile kernels: float32 (complex64), native float64, or
 // double-float pairs on the FP32 units (complex128).
-enum ArithKind { AK_FP32 = 0, AK_FP64 = 1, AK_DF64 = 2, AK_TC = 3 };
+// AK_TC: complex128 digit products on the tensor cores; AK_TC32: complex64
+// bfloat16 triple split on the tensor cores.
+enum ArithKind { AK_FP32 = 0, AK_FP64 = 1, AK_DF64 = 2, AK_TC = 3, AK_TC32 = 4 };
 
 struct Machine {           // throughput model used by the autotuner (measured on GB300)
     double hbm_Bps = 6.6e12;
@@ -69,6 +71,7 @@ struct Machine {           // throughput model used by the autotuner (measured o
     double fp64_ips = 4.6e11;   // FP64 lane instructions per second
     double smem_Bps = 3.5e13;
     double mma_flops = 5.8e14;  // bfloat16 mma.sync, dense
+    double tc05_flops = 1.2e15; // tcgen05 16-bit MMAs as issued by the tile pass (about 60 % of peak)
     double launch_s = 4e-6;
 };
 

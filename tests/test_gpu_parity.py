@@ -486,10 +486,15 @@ def test_auto_arith_falls_back_for_unnormalised_amplitudes(sv):
 
 
 def test_auto_arith_threshold(sv):
-    """SV_ARITH_AUTO: double-float below 19 qubits, tcgen05 digits from 19 on."""
+    """SV_ARITH_AUTO: below 19 qubits double-float (complex128) / float32 FMAs
+    (complex64), tcgen05 from 19 on."""
     for n, want in ((18, sv.ARITH_DF64), (19, sv.ARITH_TC)):
         g = _random_circuit(n, 40, 700 + n)
         st = _check(sv, n, "c128", g)
+        assert st["arith"] == want, (n, st["arith"])
+    for n, want in ((18, sv.ARITH_NATIVE), (19, sv.ARITH_TC)):  # complex64: float32 FMAs / triple split
+        g = _random_circuit(n, 40, 800 + n)
+        st = _check(sv, n, "c64", g)
         assert st["arith"] == want, (n, st["arith"])
 
 
@@ -516,3 +521,56 @@ def test_tc_bounded_wait_reports_timeout_and_recovers(sv):
         assert np.abs(s.amplitudes() - ref).max() <= 1e-12
     # a fresh handle on the same context works as well
     _check(sv, n, "c128", g, ref, arith=sv.ARITH_TC)
+
+
+# ---------------------------------------------------------------------------
+# complex64 on the tensor cores (SV_ARITH_TC: bfloat16 triple split)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("n,tile", [(10, 0), (16, 10), (20, 0)])
+def test_tc32_random_circuits(sv, n, tile, k):
+    g = _random_circuit(n, 120, 5000 * n + k)
+    st = _check(sv, n, "c64", g, max_fuse_k=k, tile_qubits=tile, arith=sv.ARITH_TC)
+    assert st["arith"] == sv.ARITH_TC
+
+
+@pytest.mark.parametrize("tile", [10, 11, 12, 13, 14])
+def test_tc32_tile_sizes(sv, tile):
+    n = 17
+    g = _random_circuit(n, 150, 77 + tile)
+    ref = oracle.run(n, g)
+    for k in (3, 4, 5):
+        st = _check(sv, n, "c64", g, ref, max_fuse_k=k, tile_qubits=tile, arith=sv.ARITH_TC)
+        assert st["tile_qubits"] == tile and st["arith"] == sv.ARITH_TC
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_tc32_every_gate_on_every_operand(sv, n):
+    prep = _random_circuit(n, 3 * n, 37 + n, ops=[W.U3, W.CX])
+    rows = []
+    for op in range(14):
+        for q0 in range(n):
+            if op >= W.CX:
+                rows += [(op, q0, q1, 0.41 + q0 - 0.13 * q1) for q1 in range(n) if q1 != q0]
+            else:
+                rows.append((op, q0, -1, 0.2 + 0.6 * q0, -1.3 + q0, 2.1 - q0))
+    g = W.concat(prep, W.gates(rows))
+    ref = oracle.run(n, g)
+    for k in (1, 3, 4, 5):
+        _check(sv, n, "c64", g, ref, max_fuse_k=k, arith=sv.ARITH_TC)
+
+
+def test_tc32_accuracy_matches_float32(sv):
+    """The triple split carries float32 accuracy: on a 20-qubit circuit its
+    error against the complex128 oracle is of the same order as the FP32
+    FMA path's (relative L2 error, and max |delta a| well inside 1e-5)."""
+    n = 20
+    g = W.workload_ghz_brickwork(n, 12, 9)
+    ref = oracle.run(n, g)
+    errs = {}
+    for arith in (sv.ARITH_NATIVE, sv.ARITH_TC):
+        amp, _, _, st = _run(sv, n, "c64", g, arith=arith)
+        assert st["arith"] == arith
+        errs[arith] = (np.linalg.norm(amp - ref) / np.linalg.norm(ref), np.abs(amp - ref).max())
+    assert errs[sv.ARITH_TC][1] <= 1e-6, errs
+    assert errs[sv.ARITH_TC][0] <= 8 * max(errs[sv.ARITH_NATIVE][0], 1e-7), errs
