@@ -99,7 +99,7 @@ typedef struct {
  * compute in float32 FMAs; SV_ARITH_TC splits every float32 component into
  * three bfloat16 parts and forms the six part products of float32 accuracy
  * on the tensor cores (tcgen05.mma, float32 accumulation in tensor memory);
- * SV_ARITH_AUTO takes SV_ARITH_TC from 19 qubits on.  No magnitude limit. */
+ * SV_ARITH_AUTO takes SV_ARITH_TC from 23 qubits on.  No magnitude limit. */
 typedef enum {
     SV_ARITH_AUTO = 0,
     SV_ARITH_NATIVE = 1,

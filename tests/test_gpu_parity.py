@@ -486,13 +486,14 @@ def test_auto_arith_falls_back_for_unnormalised_amplitudes(sv):
 
 
 def test_auto_arith_threshold(sv):
-    """SV_ARITH_AUTO: below 19 qubits double-float (complex128) / float32 FMAs
-    (complex64), tcgen05 from 19 on."""
+    """SV_ARITH_AUTO: complex128 below 19 qubits in double-float, tcgen05
+    digits from 19 on; complex64 below 23 qubits in float32 FMAs, tcgen05
+    triple split from 23 on."""
     for n, want in ((18, sv.ARITH_DF64), (19, sv.ARITH_TC)):
         g = _random_circuit(n, 40, 700 + n)
         st = _check(sv, n, "c128", g)
         assert st["arith"] == want, (n, st["arith"])
-    for n, want in ((18, sv.ARITH_NATIVE), (19, sv.ARITH_TC)):  # complex64: float32 FMAs / triple split
+    for n, want in ((22, sv.ARITH_NATIVE), (23, sv.ARITH_TC)):  # complex64: float32 FMAs / triple split
         g = _random_circuit(n, 40, 800 + n)
         st = _check(sv, n, "c64", g)
         assert st["arith"] == want, (n, st["arith"])
