@@ -444,6 +444,12 @@ def main():
     roof["traffic"] = ncu_traffic(wl_key, 1.0)
     roof["hbm_gbs_per_launch"] = round(hbm_achieved, 1)
     roof["frac_of_hbm_peak"] = round(hbm_achieved / peaks["hbm_gbs"], 4)
+    hbm_bound_ms = passes * 2 * state_bytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    tensor_bound_ms = s0["tensor_flops"] / (peaks.get("bf16_tflops", 1900.0) * 1e12) * 1e3
+    bound_ms = max(hbm_bound_ms, tensor_bound_ms)
+    circuit_bound = {"passes": passes, "hbm_bound_ms": round(hbm_bound_ms, 2),
+                     "tensor_bound_ms": round(tensor_bound_ms, 2), "bound_ms": round(bound_ms, 2),
+                     "kernel_ms_per_circuit": round(kern_ms, 2), "frac_of_bound": round(bound_ms / kern_ms, 4)}
 
     out = {"metric": "statevector HBM GB/s vs peak at 30q c128", "value": round(value, 2), "unit": "GB/s",
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
@@ -460,6 +466,10 @@ def main():
            "frac_of_measured_hbm": round(value / peaks["hbm_gbs"], 4),
            "frac_of_8tbs": round(value / 8000.0, 4),
            "gate_equivalent_gbs": round(world * len(gates) * 2 * state_bytes / (ms / 1e3) / 1e9, 1),
+           # the metric counts the passes the plan needs, so a plan with fewer
+           # passes reads lower at equal speed: the circuit time against its
+           # lower bound (pass bytes at the HBM peak, MMA work at the tensor peak)
+           "circuit_bound": circuit_bound,
            "roofline": roof,
            "e2e": {"value": round(e2e_val, 2), "unit": "GB/s", "ms_per_step": round(e2e_ms, 3),
                    "h2d_bytes_per_step": int(s0["upload_bytes"]), "d2h_bytes_per_step": (1 << n) * 8},

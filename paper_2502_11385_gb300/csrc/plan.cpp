@@ -172,6 +172,31 @@ void finalize(std::vector<Block>& blocks, const sv_gate* g) {
     }
 }
 
+// The blocks (in list order) that can run in one pass whose tile holds the
+// qubits of `local`: a dense block joins when its qubits are local, a
+// diagonal block always; a block that cannot join blocks its qubits for
+// every later block of the pass.  Returns the dense work joined (sum of 2^k).
+static double pass_with(const std::vector<Block>& blocks, const std::vector<char>& done, size_t first,
+                        uint64_t local, std::vector<int>* out) {
+    uint64_t blocked = 0;
+    double work = 0;
+    for (size_t b = first; b < blocks.size(); b++) {
+        if (done[b]) continue;
+        const Block& B = blocks[b];
+        if (B.mask & blocked) {
+            blocked |= B.mask;
+            continue;
+        }
+        if (B.kind == BK_DIAG || (B.mask & ~local) == 0) {
+            if (out) out->push_back((int)b);
+            if (B.kind != BK_DIAG) work += (double)(1 << B.k);
+        } else {
+            blocked |= B.mask;
+        }
+    }
+    return work;
+}
+
 std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, int coalesce) {
     std::vector<Pass> passes;
     const size_t nb = blocks.size();
@@ -186,33 +211,44 @@ std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, 
         if (nb) passes.push_back(p);
         return passes;
     }
-    const uint64_t low = (1ull << std::min(coalesce, n)) - 1;
+    const int c = std::min(coalesce, n);
+    const uint64_t low = (1ull << c) - 1;
+    auto fill = [&](uint64_t local) {  // up to tile_m qubits with the lowest unused ones
+        for (int q = 0; q < n && popc(local) < tile_m; q++) local |= 1ull << q;
+        return local;
+    };
     while (first < nb) {
-        Pass p;
+        // candidate 1: greedy, the tile grows with the blocks in list order
         uint64_t local = low, blocked = 0;
         for (size_t b = first; b < nb; b++) {
             if (done[b]) continue;
             const Block& B = blocks[b];
-            if (B.mask & blocked) { blocked |= B.mask; continue; }
-            if (B.kind == BK_DIAG) { p.blocks.push_back((int)b); done[b] = 1; continue; }
-            uint64_t need = local | B.mask;
-            if (popc(need) <= tile_m) {
-                local = need;
-                p.blocks.push_back((int)b);
-                done[b] = 1;
-            } else {
+            if (B.mask & blocked) {
                 blocked |= B.mask;
-            }
-            if ((blocked | local) == all && popc(local) == tile_m) {
-                // every qubit is either blocked or local and the tile is full:
-                // only diagonal blocks on unblocked qubits could still join
                 continue;
             }
+            if (B.kind == BK_DIAG) continue;
+            const uint64_t need = local | B.mask;
+            if (popc(need) <= tile_m) local = need;
+            else blocked |= B.mask;
         }
-        // fill the tile up to tile_m qubits with the lowest unused qubits
-        for (int q = 0; q < n && popc(local) < tile_m; q++) local |= 1ull << q;
-        p.local_mask = local;
-        p.m = popc(local);
+        uint64_t best = fill(local);
+        double best_work = pass_with(blocks, done, first, best, nullptr);
+        // candidates 2: the low qubits plus a contiguous window of the others
+        const int w = tile_m - c;
+        for (int s = c; w > 0 && s + w <= n; s++) {
+            const uint64_t cand = low | (((1ull << w) - 1) << s);
+            const double work = pass_with(blocks, done, first, cand, nullptr);
+            if (work > best_work) {
+                best_work = work;
+                best = cand;
+            }
+        }
+        Pass p;
+        pass_with(blocks, done, first, best, &p.blocks);
+        for (int b : p.blocks) done[b] = 1;
+        p.local_mask = best;
+        p.m = popc(best);
         passes.push_back(p);
         while (first < nb && done[first]) first++;
     }
