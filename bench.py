@@ -275,7 +275,21 @@ def run_batch_form(args):
         torch.cuda.synchronize()
         shared_ms = (time.perf_counter() - t0) * 1e3 / args.steps
         shared_err = max((a - c).abs().max().item() for a, c in zip(ref, up_o + dn_o))
-        del up_o, dn_o
+        # reconstruction (Eqs. 3.2-3.7) on the GPU: the marginal over 12 upstream
+        # and 12 downstream qubits (2^24 outputs; the 2^40 joint does not fit)
+        cut_q = list(cc.cut_qubits)
+        keep_a = sum(1 << q for q in [q for q in range(cc.width_a) if q not in cut_q][:12])
+        keep_b = (1 << 12) - 1
+        rec = torch.empty(1 << 24, dtype=torch.float64, device="cuda")
+        sv.cut_reconstruct(up_o, dn_o, cc.width_a, cut_q, cc.width_b, keep_a, keep_b, out=rec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            sv.cut_reconstruct(up_o, dn_o, cc.width_a, cut_q, cc.width_b, keep_a, keep_b, out=rec)
+        torch.cuda.synchronize()
+        rec_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        rec_norm_err = abs(rec.sum().item() - 1.0)
+        del up_o, dn_o, rec
         nv = len(items)
         out["results"].append({"dtype": dtype, "variants": nv, "batched_ms": round(batch_ms, 3),
                                "loop_ms": round(loop_ms, 3), "batched_variants_per_s": round(nv / batch_ms * 1e3, 2),
@@ -285,6 +299,9 @@ def run_batch_form(args):
                                "shared_work_variants_per_s": round(nv / shared_ms * 1e3, 2),
                                "shared_work_speedup_vs_loop": round(loop_ms / shared_ms, 3),
                                "shared_work_max_abs_dp": shared_err,
+                               "reconstruction": {"outputs": "2^24 (12 upstream + 12 downstream qubits)",
+                                                  "terms": 4 ** len(cut_q), "ms": round(rec_ms, 3),
+                                                  "abs_sum_minus_1": rec_norm_err},
                                "graph_launches": info["n_launches"], "arena_gib": round(info["arena_bytes"] / 2**30, 3),
                                "batch_build_ms": round(build_ms, 1)})
         torch.cuda.empty_cache()

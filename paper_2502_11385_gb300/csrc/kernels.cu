@@ -1278,7 +1278,7 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         smraw + (MODE == MODE_T05 ? t05::kSmemBase : (MODE == MODE_T32 ? t32::kSmemBase : 0)));
     __shared__ uint64_t dep[2][32];  // deposit tables for the tile's high local bits
     __shared__ __align__(16) DevPass P;
-    __shared__ uint64_t s_state, s_begin;
+    __shared__ uint64_t s_state, s_begin, s_next_base;
     __shared__ __align__(8) uint64_t t05_mbar;
     __shared__ uint32_t t05_tmem;
     constexpr int kOpCache = 48;  // the pass's op descriptors, read once per pass
@@ -1350,6 +1350,17 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         uint64_t base = 0;
         for (int b = 0; b < P.n - m; b++)
             if ((tl >> b) & 1) base |= 1ull << P.NL[b];
+        if (threadIdx.x == 0) {  // base of the CTA's next tile (same entry), for the L2 prefetch
+            const uint64_t tn = t + gridDim.x;
+            uint64_t bn = ~0ull;
+            if (tn < total_tiles && tn - s_begin < P.tile_count) {
+                const uint64_t tln = tn - s_begin;
+                bn = 0;
+                for (int b = 0; b < P.n - m; b++)
+                    if ((tln >> b) & 1) bn |= 1ull << P.NL[b];
+            }
+            s_next_base = bn;
+        }
         if constexpr (MODE == MODE_DF) {
             const int N = 1 << m;
             for (int j = threadIdx.x; j < N; j += blockDim.x) {
@@ -1407,16 +1418,11 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
             // Prefetch the CTA's next tile (same entry) into L2 while this one
             // is computed: one bulk prefetch per run of 2^c contiguous
             // amplitudes (256 bytes), so the next load phase reads from L2.
-            // (Measured: faster for the FP32 / FP64 / double-float passes,
-            // slower for the fixed-point tensor-core passes.)
-            const uint64_t tn = t + gridDim.x;
+            // The next tile's base comes from thread 0 (computed before the
+            // load phase), so a thread adds one address and one instruction.
             const int runs = 1 << (m - c);
-            constexpr bool kPrefetch = MODE == MODE_F32 || MODE == MODE_F64 || MODE == MODE_DF;
-            if (kPrefetch && tn < total_tiles && tn - s_begin < P.tile_count && (int)threadIdx.x < runs) {
-                const uint64_t tln = tn - s_begin;
-                uint64_t bn = 0;
-                for (int b = 0; b < P.n - m; b++)
-                    if ((tln >> b) & 1) bn |= 1ull << P.NL[b];
+            const uint64_t bn = s_next_base;
+            if (bn != ~0ull && (int)threadIdx.x < runs) {
                 const int r = threadIdx.x;
                 const Store* src = st + (bn | dep[0][r & 31] | dep[1][(r >> 5) & 31]);
                 asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"((int)(sizeof(Store) << c))
