@@ -277,9 +277,11 @@ uint16_t f16_of_int(int d) {
 
 // Block digits in the shared-memory image the tcgen05 kernel copies: B is
 // 7R x R fp16, row j R + r' = digit j of real-form row r (r' = (amp >> 2) 8 +
-// part 4 + (amp & 3) for output part 0 = re / 1 = im of amplitude amp),
-// column c = real-form column; K-major core matrices of 8 rows x 16 bytes
-// (128 bytes between core matrices along K, 16 R bytes along N).  Returns
+// part 4 + (amp & 3) for output part 0 = re / 1 = im of amplitude amp); the
+// K position of real-form column c = cp D + ca is k' = 8 (ca >> 2) + 4 cp +
+// (ca & 3), the order in which the kernel stores amplitude digits in tensor
+// memory; K-major core matrices of 8 rows x 16 bytes (128 bytes between core
+// matrices along K, 16 R bytes along N).  Returns
 // false if some level sum could exceed 2^22 in magnitude (amplitude digits
 // bounded by 256 for the top digit and 128 for the others).
 bool t05_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& out) {
@@ -297,10 +299,14 @@ bool t05_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& 
             else v = c < D ? u.imag() : u.real();
             int d[7];
             balanced_digits(q62_of(v), d);
+            // K position of real-form column c (component cp of amplitude ca):
+            // k' = 8 (ca >> 2) + 4 cp + (ca & 3)
+            const int cp = c / D, ca = c % D;
+            const int kq = 8 * (ca >> 2) + 4 * cp + (ca & 3);
             for (int j = 0; j < 7; j++) {
                 S[j] += d[j] < 0 ? -d[j] : d[j];
                 const int n = j * R + rp;
-                const size_t off = (size_t)(n >> 3) * SBO + (size_t)(c >> 3) * 128 + (n & 7) * 16 + (c & 7) * 2;
+                const size_t off = (size_t)(n >> 3) * SBO + (size_t)(kq >> 3) * 128 + (n & 7) * 16 + (kq & 7) * 2;
                 img[off / 2] = f16_of_int(d[j]);
             }
         }

@@ -656,8 +656,8 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
 
 // ---------------------------------------------------------------------------
 // K5-t05: the same digit products on the fifth-generation tensor cores
-// (tcgen05.mma issued by one thread, operands in shared memory, accumulators
-// in tensor memory).
+// (tcgen05.mma issued by one thread; amplitude digits and accumulators in
+// tensor memory, block digits in shared memory).
 //
 // Here the tile holds Q56 (v = x * 2^56, the Q62 value >> 6: the digit
 // split never used the low 6 bits) and digits are balanced:
@@ -672,31 +672,31 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
 //
 // One round covers 128 groups (one M = 128 tile; 3-qubit blocks take two
 // M-tiles per round):
-//   A_i (shared, 128 x R fp16) = digit i of the groups' R = 2^(k+1) real
-//       components, K-major core matrices of 8 rows x 16 bytes, no swizzle;
-//   B   (shared, 7R x R fp16): row j R + r' = digit j of real-form row r of
-//       the block (r' = (amp >> 2) 8 + part 4 + (amp & 3) for output
-//       component part (0 = re, 1 = im) of amplitude amp, so that one thread
-//       reads the re and im outputs of 4 amplitudes from 8 adjacent columns);
+//   A_i (tensor memory, 128 lanes x R/2 columns) = digit i of the groups'
+//       R = 2^(k+1) real components, a column holding two fp16 K-elements;
+//   B   (shared, 7R x R fp16, K-major core matrices of 8 rows x 16 bytes, no
+//       swizzle): row j R + r' = digit j of real-form row r of the block
+//       (r' = (amp >> 2) 8 + part 4 + (amp & 3) for output component part
+//       (0 = re, 1 = im) of amplitude amp, so that one thread reads the re
+//       and im outputs of 4 amplitudes from 8 adjacent columns);
 //   D   (tensor memory, 128 lanes x 7R fp32 columns): column L R + r' =
 //       level L of output r'.
 // Amplitude digit i meets block digits j = 0..6-i in one MMA of
 // N = (7 - i) R whose accumulator starts at column i R, so each level i + j
-// collects in its own columns: 7 x R/16 MMAs per M-tile and round.  Two
-// accumulator buffers (2 x 256 TMEM columns, one CTA per SM) let the MMAs of
-// round r run while the threads re-assemble round r - 1; the CTA has 512
+// collects in its own columns: 7 x R/16 MMAs per M-tile and round.  Two A
+// buffers in tensor memory (one CTA per SM holds all 512 columns) let the
+// threads split round r + 1 while the MMAs of round r run; the CTA has 512
 // threads (16 warps) to hide the latency of the digit work.
 // ---------------------------------------------------------------------------
 namespace t05 {
 
 constexpr int kThreads = 512;
 constexpr int kLogThreads = 9;
-constexpr int kABytes = 7 * 128 * 32 * 2;  // 7 digit planes of 128 x 32 fp16 (or 2 M-tiles x 7 x 128 x 16)
 constexpr int kBBytes = 14 * 32 * 32;      // 7R x R fp16 for R = 32
-constexpr int kSmemBase = kABytes + kBBytes;  // 70 KiB; the amplitude tile follows
+constexpr int kSmemBase = kBBytes;  // block digits; the amplitude tile follows (A lives in tensor memory)
 constexpr int kSmemMin = 116 * 1024;       // one CTA per SM (it holds all 512 TMEM columns)
-constexpr int kTmemCols = 512;             // two accumulator buffers
-constexpr uint32_t kTmemBuf = 256;         // column offset of the second buffer
+constexpr int kTmemCols = 512;             // the whole of an SM's tensor memory
+constexpr uint32_t kTmemBuf = 256;         // complex64 mode: column offset of the second accumulator buffer
 constexpr unsigned kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
 constexpr unsigned long long kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
 constexpr unsigned kWaitPolls = 1u << 26;                 // and after this many polls in any case
@@ -816,22 +816,32 @@ __device__ __forceinline__ void store_digits4(long long x0, long long x1, long l
 }
 
 struct Ctx {
-    unsigned char* a;  // digit planes
+    unsigned char* a;  // part planes (complex64 mode)
     unsigned char* b;  // block digits
     uint32_t a_addr, b_addr, mbar, tmem;
     uint32_t phase;
     bool failed;
 };
 
-// Dense block of 3 or 4 qubits on tcgen05 (balanced 8-bit digits, levels 0..6).
-// Bg: the block's digits in the shared-memory image (14 R^2 bytes).
+// Dense block of 3 or 4 qubits on tcgen05 (balanced 8-bit digits, levels 0..6),
+// amplitude digits (the A operand) in tensor memory.
+//
+// TMEM (512 columns): accumulator at columns [0, 256) (7R columns per M-tile,
+// M-tile mt at 128 mt), two A buffers at [256, 384) and [384, 512): digit
+// plane i of M-tile mt at (mt 7 + i) R/2, column c holding the K-elements
+// 2c (low half) and 2c + 1 of the lane's row.  K order: k' = 8 cg + 4 part + e
+// for component part of amplitude 4 cg + e (the host writes B in the same
+// order), so one thread stores its 4 amplitudes' digits as 4 adjacent
+// columns and later reads their outputs from 8 adjacent accumulator columns.
+// While the MMAs of round r run, the threads split round r + 1 into the other
+// A buffer; the (single) accumulator is re-assembled after the MMAs finish.
 template <int K>
 __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const uint4* __restrict__ Bg, Ctx& cx) {
     static_assert(K == 3 || K == 4, "tensor-core blocks have 3 or 4 qubits");
     constexpr int D = 1 << K, R = 2 * D;
-    constexpr int SBO = 16 * R;         // bytes between 8-row core groups (R / 8 core matrices of 128 B)
-    constexpr int PLANE = 128 * R * 2;  // one digit plane of one M-tile
+    constexpr int SBO = 16 * R;              // B: bytes between 8-row core groups
     constexpr int GPR = K == 3 ? 256 : 128;  // groups per round
+    constexpr uint32_t kABuf = 256;          // TMEM column of A buffer 0 (buffer 1 at +128)
     int pos[K], pm[K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
@@ -839,39 +849,47 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
         pm[j] = 1 << pos[j];
     }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // block digits: asynchronous copies, overlapped with the first digit split
     for (int i = tid; i < 14 * R * R / 16; i += kThreads) cp_async16(cx.b_addr + 16 * i, Bg + i);
     const int ng = 1 << (m - K);
-    // digit split: thread -> (M-tile, row, amplitude quartet qa); lane pairs
-    // share a row so that a warp's 8-byte stores fill whole core-matrix rows
-    const int s_row = ((tid >> 5) & 7) * 16 + (lane >> 1);
-    const int s_mt = K == 4 ? 0 : tid >> 8;
-    const int s_qa = K == 4 ? 2 * (tid >> 8) + (lane & 1) : (lane & 1);
-    // re-assembly: warp -> (TMEM lane quarter, M-tile, column group of 8 = 4 amplitudes)
-    const int e_cg = K == 4 ? warp >> 2 : (warp >> 2) & 1;
-    const int e_mt = K == 4 ? 0 : warp >> 3;
-    const int e_row = (warp & 3) * 32 + lane;
-    // Offsets fixed for the op: a group index is round base | local index
-    // (disjoint bits), insert_zero_bits maps disjoint bits to disjoint bits
-    // and the swizzle is linear over GF(2), so a slot is
-    // swz(iz(base)) ^ swz(iz(local)) ^ swz(offset of the amplitude).
-    int s_off[4], e_off[4];
+    // thread -> (TMEM lane quarter = row, M-tile, 4 amplitudes cg), for both the split and the re-assembly
+    const int cg = K == 4 ? warp >> 2 : (warp >> 2) & 1;
+    const int mt_t = K == 4 ? 0 : warp >> 3;
+    const int row = (warp & 3) * 32 + lane;
+    const uint32_t lane_bits = (uint32_t)((warp & 3) * 32) << 16;
+    int off[4];
 #pragma unroll
-    for (int e = 0; e < 4; e++) {
-        s_off[e] = swz<double>(group_offset<K>(4 * s_qa + e, pm));
-        e_off[e] = swz<double>(group_offset<K>(4 * e_cg + e, pm));
-    }
-    const int s_loc = s_mt * 128 + s_row, e_loc = e_mt * 128 + e_row;
-    const int s_sw = swz<double>(insert_zero_bits<K>(s_loc, pos));
-    const int e_sw = swz<double>(insert_zero_bits<K>(e_loc, pos));
-    // re-assembly of the round starting at group r0 from TMEM buffer tbuf
-    auto reassemble = [&](int r0, int r_mt, uint32_t tbuf) {
+    for (int e = 0; e < 4; e++) off[e] = swz<double>(group_offset<K>(4 * cg + e, pm));
+    const int loc = mt_t * 128 + row;
+    const int loc_sw = swz<double>(insert_zero_bits<K>(loc, pos));
+    auto n_mt_of = [&](int g0) { return (K == 3 && g0 + 128 < ng) ? 2 : 1; };
+    // digits of the thread's 4 amplitudes of the round at g0 into A buffer ab
+    auto split = [&](int g0, int ab) {
+        if (mt_t >= n_mt_of(g0)) return;  // warp-uniform
+        unsigned d[4][7];
+        if (g0 + loc < ng) {
+            const int bg = swz<double>(insert_zero_bits<K>(g0, pos)) ^ loc_sw;
+            Q2 v[4];
+#pragma unroll
+            for (int e = 0; e < 4; e++) v[e] = sm[bg ^ off[e]];
+            bal_digits_pair(v[0].re, v[1].re, d[0]);
+            bal_digits_pair(v[2].re, v[3].re, d[1]);
+            bal_digits_pair(v[0].im, v[1].im, d[2]);
+            bal_digits_pair(v[2].im, v[3].im, d[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 7; i++) d[0][i] = d[1][i] = d[2][i] = d[3][i] = 0u;
+        }
+        const uint32_t a0 = cx.tmem + lane_bits + kABuf + (uint32_t)ab * 128 + (uint32_t)(mt_t * 7) * (R / 2) + 4 * cg;
+#pragma unroll
+        for (int i = 0; i < 7; i++)
+            asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(a0 + i * (R / 2)),
+                         "r"(d[0][i]), "r"(d[1][i]), "r"(d[2][i]), "r"(d[3][i])
+                         : "memory");
+    };
+    auto reassemble = [&](int r0) {
         fence_after();
-        if (e_mt >= r_mt) return;  // warp-uniform
-        const uint32_t t0 = cx.tmem + tbuf + ((uint32_t)((warp & 3) * 32) << 16) + e_mt * 128 + 8 * e_cg;
-        // level words w_L = bits of (Z_L + 1.5 * 2^23) = 0x4B400000 + Z_L; pairs
-        // P = 256 Z_a + Z_b fit in int32 (|Z| <= 2^22), formed with wrapping
-        // 32-bit arithmetic: 256 w_a + w_b - 257 * 0x4B400000
+        if (mt_t >= n_mt_of(r0)) return;  // warp-uniform
+        const uint32_t t0 = cx.tmem + lane_bits + mt_t * 128 + 8 * cg;
         constexpr unsigned kPairBias = 0u - 257u * kMagicBits;
         int P[3][8];
         uint32_t a[8], b[8];
@@ -889,9 +907,8 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
         }
         ld8(t0 + 6 * R, a);
         ld_wait();
-        if (r0 + e_loc < ng) {
-            const int bg = swz<double>(insert_zero_bits<K>(r0, pos)) ^ e_sw;
-            // y = P01 2^32 + P23 2^16 + P45 + Z_6 / 256 (rounded), in Q56 units
+        if (r0 + loc < ng) {
+            const int bg = swz<double>(insert_zero_bits<K>(r0, pos)) ^ loc_sw;
             auto out = [&](int e) {
                 const int t6 = (int)(__float_as_uint(__uint_as_float(a[e]) + 12582912.0f) - kMagicBits + 128u) >> 8;
                 return (long long)(((unsigned long long)(long long)P[0][e] << 32) +
@@ -899,64 +916,55 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
                                    (unsigned long long)(long long)(P[2][e] + t6));
             };
 #pragma unroll
-            for (int e = 0; e < 4; e++)
-                sm[bg ^ e_off[e]] = Q2{out(e), out(e + 4)};
+            for (int e = 0; e < 4; e++) sm[bg ^ off[e]] = Q2{out(e), out(e + 4)};
         }
     };
-    // Rounds are pipelined over two TMEM accumulators: the MMAs of round r
-    // run while the threads re-assemble round r - 1.
-    int prev_g0 = -1, prev_mt = 0;
-    uint32_t prev_buf = 0;
-    for (int g0 = 0; g0 < ng; g0 += GPR) {
-        {
-            if (g0 + s_loc < ng) {
-                const int bg = swz<double>(insert_zero_bits<K>(g0, pos)) ^ s_sw;
-                Q2 v[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) v[e] = sm[bg ^ s_off[e]];
-                // component k = part D + 4 qa + e: k-core k >> 3, byte (k & 7) * 2
-                unsigned char* row0 = cx.a + s_mt * 7 * PLANE + (s_row >> 3) * SBO + (s_row & 7) * 16 + (s_qa & 1) * 8;
-                store_digits4(v[0].re, v[1].re, v[2].re, v[3].re, row0 + (s_qa >> 1) * 128, PLANE);
-                store_digits4(v[0].im, v[1].im, v[2].im, v[3].im, row0 + (D / 8 + (s_qa >> 1)) * 128, PLANE);
-            }
-        }
-        cp_async_wait_all();
-        fence_async_smem();
-        __syncthreads();
-        const int n_mt = (K == 3 && g0 + 128 < ng) ? 2 : 1;
-        const uint32_t buf = (uint32_t)((g0 / GPR) & 1) * kTmemBuf;
+    auto issue = [&](int g0, int ab) {
         // (OPF_TEST_NO_MMA, a test hook: nothing is issued, so the bounded wait runs out)
-        if (tid == 0 && !(op.flags & OPF_TEST_NO_MMA)) {
-            fence_after();
-            for (int mt = 0; mt < n_mt; mt++)
+        if (tid != 0 || (op.flags & OPF_TEST_NO_MMA)) return;
+        fence_after();
+        const int n_mt = n_mt_of(g0);
+        for (int mt = 0; mt < n_mt; mt++)
 #pragma unroll
-                for (int i = 0; i < 7; i++)
+            for (int i = 0; i < 7; i++)
 #pragma unroll
-                    for (int ks = 0; ks < R / 16; ks++) {
-                        const uint64_t da = desc(cx.a_addr + (mt * 7 + i) * PLANE + ks * 256, 128, SBO);
-                        const uint64_t db = desc(cx.b_addr + ks * 256, 128, SBO);
-                        mma(cx.tmem + buf + mt * 128 + i * R, da, db, idesc((7 - i) * R), (i | ks) != 0);
-                    }
-            commit(cx.mbar);
-        }
-        if (prev_g0 >= 0) reassemble(prev_g0, prev_mt, prev_buf);
+                for (int ks = 0; ks < R / 16; ks++) {
+                    const uint32_t ta = cx.tmem + kABuf + (uint32_t)ab * 128 + (uint32_t)(mt * 7 + i) * (R / 2) + ks * 8;
+                    const uint64_t db = desc(cx.b_addr + ks * 256, 128, SBO);
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(
+                            cx.tmem + mt * 128 + i * R),
+                        "r"(ta), "l"(db), "r"(idesc((7 - i) * R)), "r"((uint32_t)((i | ks) != 0))
+                        : "memory");
+                }
+        commit(cx.mbar);
+    };
+    split(0, 0);
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    cp_async_wait_all();  // the block digits
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    issue(0, 0);
+    int g0 = 0, ab = 0;
+    for (;; g0 += GPR, ab ^= 1) {
+        const int gn = g0 + GPR;
+        if (gn < ng) split(gn, ab ^ 1);  // overlaps the MMAs of round g0
         const bool ok = wait(cx.mbar, cx.phase);
         cx.phase ^= 1;
+        if (ok) reassemble(g0);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        fence_before();
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(&g_fault, 1);
             wait(cx.mbar, cx.phase ^ 1);  // give the MMAs in flight one more bounded wait
             cx.failed = true;
             return;
         }
-        fence_before();
-        __syncthreads();
-        prev_g0 = g0;
-        prev_mt = n_mt;
-        prev_buf = buf;
+        if (gn >= ng) break;
+        issue(gn, ab ^ 1);
     }
-    reassemble(prev_g0, prev_mt, prev_buf);
-    fence_before();
-    __syncthreads();
 }
 
 }  // namespace t05
@@ -1300,7 +1308,7 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         __syncthreads();
         t05::fence_after();
         cx.a = smraw;
-        cx.b = smraw + (MODE == MODE_T05 ? t05::kABytes : t32::kABytes);
+        cx.b = smraw + (MODE == MODE_T05 ? 0 : t32::kABytes);
         cx.a_addr = t05::smem_addr(cx.a);
         cx.b_addr = t05::smem_addr(cx.b);
         cx.mbar = t05::smem_addr(&t05_mbar);
