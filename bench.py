@@ -442,8 +442,12 @@ def main():
         alu_peak = SMS * FP32_FMA_PER_CLK_SM * peaks.get("sm_max_mhz", 2070.0) * 1e6
         alu_name = "FP32 152 SM x 128 lanes x max clock (lane-ops/s)"
     alu_achieved = alu_ops / (kern_ms / 1e3)
-    if arith in (3, 4) and s0["tensor_flops"] > 0:
-        # tensor-core modes: the digit products are the contraction; bf16 peak
+    # tensor-core modes: bound by the tensor pipe or by HBM, whichever the
+    # circuit's algorithmic work at the measured peaks makes slower
+    t_tensor = s0["tensor_flops"] / (peaks.get("bf16_tflops", 1900.0) * 1e12)
+    t_hbm = passes * 2 * state_bytes / (peaks["hbm_gbs"] * 1e9)
+    if arith in (3, 4) and s0["tensor_flops"] > 0 and t_tensor >= t_hbm:
+        # the digit products are the contraction; bf16 peak
         tf = s0["tensor_flops"] / (kern_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": round(tf, 2), "peak": peaks.get("bf16_tflops", 1900.0),
                 "unit": "TFLOP/s", "frac": round(tf / peaks.get("bf16_tflops", 1900.0), 4),
@@ -453,6 +457,11 @@ def main():
     elif alu_achieved / alu_peak > hbm_achieved / peaks["hbm_gbs"]:
         roof = {"bound": "alu", "achieved": round(alu_achieved / 1e12, 3), "peak": round(alu_peak / 1e12, 3),
                 "unit": "T lane-ops/s", "frac": round(alu_achieved / alu_peak, 4), "peak_source": alu_name}
+    elif arith in (3, 4) and s0["tensor_flops"] > 0:
+        tf = s0["tensor_flops"] / (kern_ms / 1e3) / 1e12
+        roof = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(hbm_achieved / peaks["hbm_gbs"], 4), "peak_source": f"{peak_src} hbm_gbs",
+                "tensor_tflops": round(tf, 2), "alu_frac": round(alu_achieved / alu_peak, 4)}
     else:
         roof = {"bound": "hbm", "achieved": round(hbm_achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(hbm_achieved / peaks["hbm_gbs"], 4), "peak_source": f"{peak_src} hbm_gbs"}

@@ -328,9 +328,11 @@ bool t05_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& 
 // Block parts for the complex64 tensor-core kernel: B is 3R x R bf16, row
 // j R + r' = part j of real-form row r (x = h + m + l, h = bf16(x),
 // m = bf16(x - h), l = bf16(x - h - m), from the float64 entry), with
-// r' = (amp / P) 2P + part P + (amp mod P), P = D / 4; column c = real-form
-// column; K-major core matrices of 8 rows x 16 bytes (128 bytes between core
-// matrices along K, 16 R bytes along N).
+// r' = (amp / P) 2P + part P + (amp mod P), P = D / 4; real-form column
+// c = cp D + ca sits at K position k' = 2P (ca / P) + P cp + (ca mod P), the
+// order in which the kernel stores amplitude parts in tensor memory; K-major
+// core matrices of 8 rows x 16 bytes (128 bytes between core matrices along
+// K, 16 R bytes along N).
 uint16_t bf16_rn(double x) {
     float f = (float)x;  // float64 -> float32 -> bfloat16, both to nearest (the parts below
     uint32_t u;          // absorb the double rounding: x - h is formed from x itself)
@@ -362,7 +364,9 @@ void t32_block_image(int k, const std::vector<svp::cd>& M, std::vector<Word16>& 
             const uint16_t parts[3] = {h, m, l};
             for (int j = 0; j < 3; j++) {
                 const int n = j * R + rp;
-                img[((size_t)(n >> 3) * SBO + (size_t)(c >> 3) * 128 + (n & 7) * 16 + (c & 7) * 2) / 2] = parts[j];
+                const int cp = c / D, ca = c % D;
+                const int kq = 2 * Pq * (ca / Pq) + Pq * cp + (ca % Pq);  // K order of the amplitude parts in TMEM
+                img[((size_t)(n >> 3) * SBO + (size_t)(kq >> 3) * 128 + (n & 7) * 16 + (kq & 7) * 2) / 2] = parts[j];
             }
         }
     }

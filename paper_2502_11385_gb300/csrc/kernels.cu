@@ -696,7 +696,6 @@ constexpr int kBBytes = 14 * 32 * 32;      // 7R x R fp16 for R = 32
 constexpr int kSmemBase = kBBytes;  // block digits; the amplitude tile follows (A lives in tensor memory)
 constexpr int kSmemMin = 116 * 1024;       // one CTA per SM (it holds all 512 TMEM columns)
 constexpr int kTmemCols = 512;             // the whole of an SM's tensor memory
-constexpr uint32_t kTmemBuf = 256;         // complex64 mode: column offset of the second accumulator buffer
 constexpr unsigned kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
 constexpr unsigned long long kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
 constexpr unsigned kWaitPolls = 1u << 26;                 // and after this many polls in any case
@@ -804,21 +803,9 @@ __device__ __forceinline__ void bal_digits_pair(long long x0, long long x1, unsi
     o[6] = h2_byte_pair<0>(lo0, lo1);
 }
 
-// Digits of 4 consecutive components of one row into the 7 digit planes
-// (8 bytes per plane: half a core-matrix row).
-__device__ __forceinline__ void store_digits4(long long x0, long long x1, long long x2, long long x3,
-                                              unsigned char* p, int plane_bytes) {
-    unsigned d01[7], d23[7];
-    bal_digits_pair(x0, x1, d01);
-    bal_digits_pair(x2, x3, d23);
-#pragma unroll
-    for (int i = 0; i < 7; i++) *reinterpret_cast<uint2*>(p + i * plane_bytes) = make_uint2(d01[i], d23[i]);
-}
-
 struct Ctx {
-    unsigned char* a;  // part planes (complex64 mode)
-    unsigned char* b;  // block digits
-    uint32_t a_addr, b_addr, mbar, tmem;
+    unsigned char* b;  // block digits / parts in shared memory
+    uint32_t b_addr, mbar, tmem;
     uint32_t phase;
     bool failed;
 };
@@ -984,17 +971,19 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
 // for float32 rounding.
 //
 // One round covers 128 groups (one M = 128 tile) for blocks of 3..5 qubits
-// (smaller blocks are padded to 3): A_i (shared, 128 x R bf16, K-major core
-// matrices of 8 rows x 16 bytes), B (shared, 3R x R bf16, row j R + r' =
-// part j of real-form row r, r' = (amp / P) 2P + part P + (amp mod P) with
-// P = D / 4 amplitudes per thread), D (TMEM, 3R columns).  Rounds are
-// pipelined over two accumulator buffers as in the complex128 mode.
+// (smaller blocks are padded to 3): A_i (tensor memory, 128 lanes x R/2
+// columns, two bf16 K-elements per column) = part i of the groups' real
+// components, B (shared, 3R x R bf16, K-major core matrices of 8 rows x 16
+// bytes: row j R + r' = part j of real-form row r, r' = (amp / P) 2P +
+// part P + (amp mod P) with P = D / 4 amplitudes per thread, columns in the
+// K order of A), D (tensor memory, 3R columns).  Two A buffers let the
+// threads split round r + 1 while the MMAs of round r run, as in the
+// complex128 mode.
 // ---------------------------------------------------------------------------
 namespace t32 {
 
-constexpr int kABytes = 3 * 128 * 64 * 2;     // 3 part planes of 128 x 64 bf16 (5-qubit blocks)
-constexpr int kBBytes = 6 * 64 * 64;          // 3R x R bf16 for R = 64
-constexpr int kSmemBase = kABytes + kBBytes;  // 72 KiB; the amplitude tile follows
+constexpr int kBBytes = 6 * 64 * 64;  // 3R x R bf16 for R = 64
+constexpr int kSmemBase = kBBytes;    // block parts; the amplitude tile follows (A lives in tensor memory)
 
 __device__ __forceinline__ uint32_t idesc(int n) {  // kind::f16, f32 accumulator, bf16 A and B, M = 128
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
@@ -1036,17 +1025,22 @@ __device__ __forceinline__ void ldN<16>(uint32_t taddr, uint32_t (&r)[16]) {
         : "memory");
 }
 
-// Dense block of 3..5 qubits on tcgen05 (bfloat16 triple split).
-// Bg: the block's parts in their shared-memory image (6 R^2 bytes).
+// Dense block of 3..5 qubits on tcgen05 (bfloat16 triple split), the
+// amplitude parts (A operand) in tensor memory: accumulator in columns
+// [0, 3R), two A buffers at 256 and 384 (part plane i at i R/2, a column
+// holding two bf16 K-elements); K order k' = 2P (amp / P) + P part +
+// (amp mod P), so a thread's P amplitudes fill P adjacent columns per part.
+// While the MMAs of round r run, the threads split round r + 1 into the other
+// A buffer; the accumulator is re-assembled after the MMAs finish.
 template <int K>
 __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, const uint4* __restrict__ Bg,
                                          t05::Ctx& cx) {
     static_assert(K >= 3 && K <= 5, "tensor-core blocks have 3 to 5 qubits");
     using namespace t05;
     constexpr int D = 1 << K, R = 2 * D;
-    constexpr int SBO = 16 * R;         // bytes between 8-row core groups
-    constexpr int PLANE = 128 * R * 2;  // one part plane
-    constexpr int P = D / 4;            // amplitudes per thread
+    constexpr int SBO = 16 * R;  // B: bytes between 8-row core groups
+    constexpr int P = D / 4;     // amplitudes per thread
+    constexpr uint32_t kABuf = 256;
     int pos[K], pm[K];
 #pragma unroll
     for (int j = 0; j < K; j++) {
@@ -1056,107 +1050,97 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int i = tid; i < 6 * R * R / 16; i += kThreads) cp_async16(cx.b_addr + 16 * i, Bg + i);
     const int ng = 1 << (m - K);
-    // split: thread -> (row, amplitude group qa of P amplitudes); the lanes of a
-    // warp fill whole core-matrix rows with their stores
-    int s_row, s_qa;
-    if (K == 5) {
-        s_row = tid & 127;
-        s_qa = tid >> 7;
-    } else if (K == 4) {
-        s_row = ((tid >> 5) & 7) * 16 + (lane >> 1);
-        s_qa = 2 * (tid >> 8) + (lane & 1);
-    } else {
-        s_row = tid >> 2;
-        s_qa = tid & 3;
-    }
-    // re-assembly: warp -> (TMEM lane quarter, column group of 2P = P amplitudes)
-    const int e_cg = warp >> 2;
-    const int e_row = (warp & 3) * 32 + lane;
-    int s_off[P], e_off[P];
+    const int cg = warp >> 2;
+    const int row = (warp & 3) * 32 + lane;
+    const uint32_t lane_bits = (uint32_t)((warp & 3) * 32) << 16;
+    int off[P];
 #pragma unroll
-    for (int e = 0; e < P; e++) {
-        s_off[e] = swz<float>(group_offset<K>(P * s_qa + e, pm));
-        e_off[e] = swz<float>(group_offset<K>(P * e_cg + e, pm));
-    }
-    const int s_sw = swz<float>(insert_zero_bits<K>(s_row, pos));
-    const int e_sw = swz<float>(insert_zero_bits<K>(e_row, pos));
-    // component k = part D + P qa + e: k-core k >> 3, byte (k & 7) * 2
-    unsigned char* const a_row = cx.a + (s_row >> 3) * SBO + (s_row & 7) * 16;
-    const int k_re = P * s_qa, k_im = D + P * s_qa;
-    unsigned char* const a_re = a_row + (k_re >> 3) * 128 + (k_re & 7) * 2;
-    unsigned char* const a_im = a_row + (k_im >> 3) * 128 + (k_im & 7) * 2;
-    auto split = [&](int g0) {
-        if (g0 + s_row >= ng) return;
-        const int bg = swz<float>(insert_zero_bits<K>(g0, pos)) ^ s_sw;
-        Cx<float> v[P];
-#pragma unroll
-        for (int e = 0; e < P; e++) v[e] = sm[bg ^ s_off[e]];
+    for (int e = 0; e < P; e++) off[e] = swz<float>(group_offset<K>(P * cg + e, pm));
+    const int row_sw = swz<float>(insert_zero_bits<K>(row, pos));
+    auto split = [&](int g0, int ab) {
         unsigned h[2][P / 2], mm[2][P / 2], l[2][P / 2];
+        if (g0 + row < ng) {
+            const int bg = swz<float>(insert_zero_bits<K>(g0, pos)) ^ row_sw;
+            Cx<float> v[P];
 #pragma unroll
-        for (int e = 0; e < P / 2; e++) {
-            bf3_pair(v[2 * e].re, v[2 * e + 1].re, h[0][e], mm[0][e], l[0][e]);
-            bf3_pair(v[2 * e].im, v[2 * e + 1].im, h[1][e], mm[1][e], l[1][e]);
-        }
+            for (int e = 0; e < P; e++) v[e] = sm[bg ^ off[e]];
 #pragma unroll
-        for (int part = 0; part < 2; part++) {
-            unsigned char* p = part ? a_im : a_re;
-            if constexpr (P == 8) {
-                *reinterpret_cast<uint4*>(p) = make_uint4(h[part][0], h[part][1], h[part][2], h[part][3]);
-                *reinterpret_cast<uint4*>(p + PLANE) = make_uint4(mm[part][0], mm[part][1], mm[part][2], mm[part][3]);
-                *reinterpret_cast<uint4*>(p + 2 * PLANE) = make_uint4(l[part][0], l[part][1], l[part][2], l[part][3]);
-            } else if constexpr (P == 4) {
-                *reinterpret_cast<uint2*>(p) = make_uint2(h[part][0], h[part][1]);
-                *reinterpret_cast<uint2*>(p + PLANE) = make_uint2(mm[part][0], mm[part][1]);
-                *reinterpret_cast<uint2*>(p + 2 * PLANE) = make_uint2(l[part][0], l[part][1]);
-            } else {
-                *reinterpret_cast<unsigned*>(p) = h[part][0];
-                *reinterpret_cast<unsigned*>(p + PLANE) = mm[part][0];
-                *reinterpret_cast<unsigned*>(p + 2 * PLANE) = l[part][0];
+            for (int e = 0; e < P / 2; e++) {
+                bf3_pair(v[2 * e].re, v[2 * e + 1].re, h[0][e], mm[0][e], l[0][e]);
+                bf3_pair(v[2 * e].im, v[2 * e + 1].im, h[1][e], mm[1][e], l[1][e]);
             }
+        } else {
+#pragma unroll
+            for (int e = 0; e < P / 2; e++) h[0][e] = h[1][e] = mm[0][e] = mm[1][e] = l[0][e] = l[1][e] = 0u;
         }
+        const uint32_t a0 = cx.tmem + lane_bits + kABuf + (uint32_t)ab * 128 + P * cg;
+        auto st = [&](uint32_t ta, const unsigned (&re)[P / 2], const unsigned (&im)[P / 2]) {
+            if constexpr (P == 8)
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(ta),
+                             "r"(re[0]), "r"(re[1]), "r"(re[2]), "r"(re[3]), "r"(im[0]), "r"(im[1]), "r"(im[2]),
+                             "r"(im[3])
+                             : "memory");
+            else if constexpr (P == 4)
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};\n" ::"r"(ta), "r"(re[0]),
+                             "r"(re[1]), "r"(im[0]), "r"(im[1])
+                             : "memory");
+            else
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1,%2};\n" ::"r"(ta), "r"(re[0]), "r"(im[0])
+                             : "memory");
+        };
+        st(a0, h[0], h[1]);
+        st(a0 + R / 2, mm[0], mm[1]);
+        st(a0 + R, l[0], l[1]);
     };
-    auto reassemble = [&](int r0, uint32_t tbuf) {
+    auto reassemble = [&](int r0) {
         fence_after();
-        const uint32_t t0 = cx.tmem + tbuf + ((uint32_t)((warp & 3) * 32) << 16) + 2 * P * e_cg;
+        const uint32_t t0 = cx.tmem + lane_bits + 2 * P * cg;
         uint32_t z0[2 * P], z1[2 * P], z2[2 * P];
         ldN<2 * P>(t0, z0);
         ldN<2 * P>(t0 + R, z1);
         ldN<2 * P>(t0 + 2 * R, z2);
         ld_wait();
-        if (r0 + e_row < ng) {
-            const int bg = swz<float>(insert_zero_bits<K>(r0, pos)) ^ e_sw;
+        if (r0 + row < ng) {
+            const int bg = swz<float>(insert_zero_bits<K>(r0, pos)) ^ row_sw;
             auto y = [&](int c) {
                 return (__uint_as_float(z2[c]) + __uint_as_float(z1[c])) + __uint_as_float(z0[c]);
             };
 #pragma unroll
-            for (int e = 0; e < P; e++) sm[bg ^ e_off[e]] = Cx<float>{y(e), y(P + e)};
+            for (int e = 0; e < P; e++) sm[bg ^ off[e]] = Cx<float>{y(e), y(P + e)};
         }
     };
-    auto issue = [&](int g0) {
+    auto issue = [&](int ab) {
         if (tid != 0 || (op.flags & OPF_TEST_NO_MMA)) return;
         fence_after();
-        const uint32_t buf = (uint32_t)((g0 >> 7) & 1) * kTmemBuf;
 #pragma unroll
         for (int i = 0; i < 3; i++)
 #pragma unroll
             for (int ks = 0; ks < R / 16; ks++) {
-                const uint64_t da = desc(cx.a_addr + i * PLANE + ks * 256, 128, SBO);
+                const uint32_t ta = cx.tmem + kABuf + (uint32_t)ab * 128 + i * (R / 2) + ks * 8;
                 const uint64_t db = desc(cx.b_addr + ks * 256, 128, SBO);
-                mma(cx.tmem + buf + i * R, da, db, idesc((3 - i) * R), (i | ks) != 0);
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(cx.tmem + i * R),
+                    "r"(ta), "l"(db), "r"(idesc((3 - i) * R)), "r"((uint32_t)((i | ks) != 0))
+                    : "memory");
             }
         commit(cx.mbar);
     };
-    // the MMAs of round r run while the threads re-assemble round r - 1
-    int g0 = 0;
-    for (;; g0 += 128) {
-        split(g0);
-        cp_async_wait_all();
-        fence_async_smem();
-        __syncthreads();
-        issue(g0);
-        if (g0 > 0) reassemble(g0 - 128, (uint32_t)(((g0 - 128) >> 7) & 1) * kTmemBuf);
+    split(0, 0);
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    cp_async_wait_all();
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    issue(0);
+    int g0 = 0, ab = 0;
+    for (;; g0 += 128, ab ^= 1) {
+        const int gn = g0 + 128;
+        if (gn < ng) split(gn, ab ^ 1);  // overlaps the MMAs of round g0
         const bool ok = wait(cx.mbar, cx.phase);
         cx.phase ^= 1;
+        if (ok) reassemble(g0);
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
         fence_before();
         if (__syncthreads_or(!ok)) {
             if (tid == 0) atomicExch(&g_fault, 1);
@@ -1164,11 +1148,9 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
             cx.failed = true;
             return;
         }
-        if (g0 + 128 >= ng) break;
+        if (gn >= ng) break;
+        issue(ab ^ 1);
     }
-    reassemble(g0, (uint32_t)((g0 >> 7) & 1) * kTmemBuf);
-    fence_before();
-    __syncthreads();
 }
 
 }  // namespace t32
@@ -1281,7 +1263,7 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
     using Smem = typename Tr::Smem;
     using SwzT = typename Tr::SwzT;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    // tcgen05 modes: digit / part planes and block digits first, the tile after them
+    // tcgen05 modes: block digits / parts first, the tile after them
     Smem* sm = reinterpret_cast<Smem*>(
         smraw + (MODE == MODE_T05 ? t05::kSmemBase : (MODE == MODE_T32 ? t32::kSmemBase : 0)));
     __shared__ uint64_t dep[2][32];  // deposit tables for the tile's high local bits
@@ -1307,9 +1289,7 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         t05::fence_before();
         __syncthreads();
         t05::fence_after();
-        cx.a = smraw;
-        cx.b = smraw + (MODE == MODE_T05 ? 0 : t32::kABytes);
-        cx.a_addr = t05::smem_addr(cx.a);
+        cx.b = smraw;
         cx.b_addr = t05::smem_addr(cx.b);
         cx.mbar = t05::smem_addr(&t05_mbar);
         cx.tmem = t05_tmem;
