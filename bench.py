@@ -179,13 +179,28 @@ def cpu_baseline(n, gates, seconds, state_bytes_c128):
                       f"complex128 state ({dt:.1f} s); GB/s = gates x 2 x state bytes / time"}
 
 
+def workload_gates(args, W):
+    """The full form's circuit and its name (the same for both arms)."""
+    n = args.n
+    if args.circuit == "qaoa":
+        gates = W.workload_qaoa(n, 2, 3)[0]
+        name = f"{n}q QAOA p=2 seed 3 on a random 3-regular graph ({len(gates)} gates)"
+    elif args.circuit == "brickwork":
+        gates = W.brickwork(n, args.depth, 1)
+        name = f"{n}q brickwork depth {args.depth} seed 1 ({len(gates)} gates)"
+    else:
+        gates = W.workload_ghz_brickwork(n, args.depth, 2)
+        name = f"{n}q GHZ + brickwork depth {args.depth} seed 2 ({len(gates)} gates)"
+    return gates, name
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2502_11385_gb300 import workloads as W
     import oracle
-    gates = W.workload_ghz_brickwork(args.n, args.depth, 2)
+    gates, wl_name = workload_gates(args, W)
     per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
     last = None
@@ -198,8 +213,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": "statevector HBM GB/s vs peak at 30q c128", "value": round(v, 3),
            "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"{args.n}q GHZ + brickwork depth {args.depth} seed 2, complex128",
-                      "n_qubits": args.n},
+           "config": {"workload": f"{wl_name}, complex128", "n_qubits": args.n, "state_dtype": "c128",
+                      "arith": "oracle: complex128 gate by gate on the host cores"},
            "cpu_baseline": {"kind": "oracle", "cores": last["cores"], "sample": last["sample"], "value": round(v, 3),
                             "unit": "GB/s"},
            "e2e": {"value": round(v, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -361,15 +376,7 @@ def main():
             dist.barrier()
 
     n, dt = args.n, args.dtype
-    if args.circuit == "qaoa":
-        gates = W.workload_qaoa(n, 2, 3)[0]
-        wl_name = f"{n}q QAOA p=2 seed 3 on a random 3-regular graph ({len(gates)} gates)"
-    elif args.circuit == "brickwork":
-        gates = W.brickwork(n, args.depth, 1)
-        wl_name = f"{n}q brickwork depth {args.depth} seed 1 ({len(gates)} gates)"
-    else:
-        gates = W.workload_ghz_brickwork(n, args.depth, 2)
-        wl_name = f"{n}q GHZ + brickwork depth {args.depth} seed 2 ({len(gates)} gates)"
+    gates, wl_name = workload_gates(args, W)
     ctype = torch.complex128 if dt == "c128" else torch.complex64
     amp_bytes = 16 if dt == "c128" else 8
     state_bytes = (1 << n) * amp_bytes
@@ -481,9 +488,8 @@ def main():
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if dt == "c128" else "f32", "data": "synthetic",
-           "config": {"workload": f"{wl_name}, "
-                                  f"complex{128 if dt == 'c128' else 64}, "
-                                  + (f"fusion k<={args.fuse}" if args.fuse else "fusion k<=5 autotuned"),
+           "config": {"workload": f"{wl_name}, complex{128 if dt == 'c128' else 64}",
+                      "fusion": f"k<={args.fuse}" if args.fuse else "k<=5 autotuned",
                       "n_qubits": n, "state_dtype": dt, "arith": ({3: "tcgen05-bf16x3"}.get(arith, "fp32") if dt == "c64" else
                                 {1: "native-fp64", 2: "df64", 3: "tcgen05-digits", 4: "mma-sync-digits"}.get(arith, "df64")),
                       "fuse_k": s0["fuse_k"], "tile_qubits": s0["tile_qubits"], "passes": passes,
