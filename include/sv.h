@@ -177,7 +177,10 @@ int sv_apply_circuit(sv_state* s, const sv_gate* gates, size_t n_gates,
 /* p_i = |a_i|^2 for all 2^n amplitudes, computed and written as float64
  * (complex64 amplitudes are squared exactly, without first rounding to
  * float32).  out_len must equal 2^n (else SV_ERR_SIZE).  out is host memory
- * unless out_is_device.  Listing 3's probabilities() call. */
+ * unless out_is_device.  Page-locked host memory (cudaHostAlloc, or
+ * registered and mapped) is written by the kernel directly over the host
+ * link; pageable host memory goes through a 128 MiB device staging buffer.
+ * Listing 3's probabilities() call. */
 int sv_probabilities(sv_state* s, double* out, size_t out_len, int out_is_device);
 
 /* Marginal distribution over the qubits set in qubit_mask: out[k] is the sum

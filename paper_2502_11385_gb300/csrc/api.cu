@@ -771,7 +771,16 @@ int sv_probabilities(sv_state* s, double* out, size_t out_len, int out_is_device
         SV_TRY(cudaStreamSynchronize(s->stream));
         return SV_OK;
     }
-    // host output: through a bounded device staging buffer, chunk by chunk
+    // page-locked host output mapped into the device's address space: the kernel
+    // stores into it directly over the host link, no staging copy
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, out) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        SV_TRY(svk::launch_probs(s->dt, s->amp, 0, dim, (double*)pa.devicePointer, s->stream, s->di));
+        SV_TRY(cudaStreamSynchronize(s->stream));
+        return SV_OK;
+    }
+    (void)cudaGetLastError();
+    // pageable host output: through a bounded device staging buffer, chunk by chunk
     const uint64_t chunk = std::min<uint64_t>(dim, 1ull << 24);
     SV_TRY(ensure(&s->d_red, &s->d_red_cap, chunk * sizeof(double), false));
     for (uint64_t i0 = 0; i0 < dim; i0 += chunk) {

@@ -169,6 +169,28 @@ def test_reset_basis_and_set_amplitudes(sv):
         assert np.abs(s.amplitudes() - oracle.apply(n, v.copy(), g)).max() <= 1e-12
 
 
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_probabilities_pinned_pageable_and_device_outputs_agree(sv, dtype):
+    """The three output routes (kernel stores into mapped page-locked host
+    memory, staged copy into pageable memory, device buffer) give the same
+    bits; n = 25 spans two 128 MiB staging chunks."""
+    import torch
+    n = 25
+    g = W.concat(W.ghz_prefix(n), W.brickwork(n, 2, seed=4))
+    with sv.State(n, dtype) as s:
+        s.apply_circuit(g)
+        dev = torch.full((1 << n,), -1.0, dtype=torch.float64, device="cuda")
+        s.probabilities(dev)
+        pinned = torch.full((1 << n,), -1.0, dtype=torch.float64, pin_memory=True)
+        s.probabilities(pinned.numpy())
+        pageable = s.probabilities()
+        d = dev.cpu().numpy()
+        assert np.array_equal(pinned.numpy(), d)
+        assert np.array_equal(pageable, d)
+        assert abs(math.fsum(d) - 1.0) <= NORM_TOL[dtype]
+        assert d.min() >= 0.0
+
+
 def test_errors_leave_state_untouched(sv):
     n = 6
     with sv.State(n, "c64") as s:
