@@ -662,13 +662,15 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
 // Here the tile holds Q56 (v = x * 2^56, the Q62 value >> 6: the digit
 // split never used the low 6 bits) and digits are balanced:
 // v = sum_j X_j 256^(6 - j) with
-// |X_0| <= 256 and X_j in [-128, 127] for j >= 1 (the bytes of
-// v + 0x808080808080, minus 128), and held as float16, exact for integers
-// below 2^11: one byte permute and one logic op place two bytes b in the
-// mantissas of 1024 + b, one packed half subtraction removes 1024 + 128.  For
-// a unitary block every level sum then stays below 2^21.5 (the host checks
-// the bound 2^22 per block), so a level becomes an integer with one float
-// add: the bits of z + 1.5 * 2^23 are 0x4B400000 + z.
+// |X_0| <= 256 and X_j in [-128, 127] for j >= 1 (bytes 0..5 of
+// u = v + 2^56 + 0x808080808080, minus 128; its top 16 bits are X_0 + 256, in
+// 0..512), and held as float16, exact for integers below 2^11: byte permutes
+// place two such values b in the mantissas of 1024 + b, one packed half
+// subtraction removes 1024 + 128 (1024 + 256 for X_0).  For a unitary block
+// every level sum then stays below 2^21.5 (the host checks the bound 2^22 per
+// block), so a level becomes an integer with one float add: the bits of
+// z + 1.5 * 2^23 are 0x4B400000 + z.  The digit work is bound by the SM's
+// integer pipe, so the re-assembly keeps to float adds and multiply-adds.
 //
 // One round covers 128 groups (one M = 128 tile; 3-qubit blocks take two
 // M-tiles per round):
@@ -779,29 +781,68 @@ __device__ __forceinline__ unsigned sub_h2(unsigned a, unsigned b) {
     return d;
 }
 
-// Byte k of w0 and of w1 as balanced fp16 digits (b - 128), packed.
-template <int K8>
-__device__ __forceinline__ unsigned h2_byte_pair(unsigned w0, unsigned w1) {
-    constexpr unsigned sel = K8 | (K8 << 4) | ((4 + K8) << 8) | ((4 + K8) << 12);
-    const unsigned t = (__byte_perm(w0, w1, sel) & 0x00FF00FFu) | 0x64006400u;  // fp16 1024 + byte, twice
-    return sub_h2(t, 0x64806480u);                                            // minus 1024 + 128
+__device__ __forceinline__ unsigned long long mad_wide(unsigned a, unsigned b, unsigned long long c) {
+    unsigned long long d;
+    asm("mad.wide.u32 %0, %1, %2, %3;\n" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+    return d;
+}
+
+// u = x + 2^56 + 0x808080808080 (mod 2^64) as one wide multiply-add.
+__device__ __forceinline__ unsigned long long digit_bias(long long x) {
+    const unsigned lo = (unsigned)x, hi = (unsigned)((unsigned long long)x >> 32);
+    return mad_wide(lo, 1u, ((unsigned long long)(hi + 0x01008080u) << 32) | 0x80808080u);
+}
+
+// Two bytes b, b' (bytes 2k and 2k + 1 of m) as fp16 1024 + b, 1024 + b':
+// the exponent bytes come from the constant.
+template <int K>
+__device__ __forceinline__ unsigned h2_pair(unsigned m) {
+    return __byte_perm(m, 0x64646464u, K == 0 ? 0x4140 : 0x4342);
 }
 
 // The seven balanced digits of two Q56 values, packed pairwise as fp16 x 2.
 __device__ __forceinline__ void bal_digits_pair(long long x0, long long x1, unsigned (&o)[7]) {
-    const long long u0 = x0 + 0x808080808080ll, u1 = x1 + 0x808080808080ll;
-    const unsigned lo0 = (unsigned)u0, hi0 = (unsigned)((unsigned long long)u0 >> 32);
-    const unsigned lo1 = (unsigned)u1, hi1 = (unsigned)((unsigned long long)u1 >> 32);
-    // top digit d (|d| <= 256): fp16 bits of 1536 + d are 0x6600 + d
-    const unsigned t0 = 0x6600u + (unsigned)((int)hi0 >> 16), t1 = 0x6600u + (unsigned)((int)hi1 >> 16);
-    o[0] = sub_h2(__byte_perm(t0, t1, 0x5410), 0x66006600u);
-    o[1] = h2_byte_pair<1>(hi0, hi1);  // byte 5 of u
-    o[2] = h2_byte_pair<0>(hi0, hi1);  // byte 4
-    o[3] = h2_byte_pair<3>(lo0, lo1);
-    o[4] = h2_byte_pair<2>(lo0, lo1);
-    o[5] = h2_byte_pair<1>(lo0, lo1);
-    o[6] = h2_byte_pair<0>(lo0, lo1);
+    const unsigned long long u0 = digit_bias(x0), u1 = digit_bias(x1);
+    const unsigned lo0 = (unsigned)u0, hi0 = (unsigned)(u0 >> 32);
+    const unsigned lo1 = (unsigned)u1, hi1 = (unsigned)(u1 >> 32);
+    // top digit plus 256 (0..512): the top 16 bits of u, under the exponent of 1024
+    o[0] = sub_h2(__byte_perm(hi0, hi1, 0x7632) | 0x64006400u, 0x65006500u);
+    // bytes of the two values interleaved, then one permute per digit
+    const unsigned mh = __byte_perm(hi0, hi1, 0x5140);  // bytes 4, 5
+    const unsigned m1 = __byte_perm(lo0, lo1, 0x7362);  // bytes 2, 3
+    const unsigned m0 = __byte_perm(lo0, lo1, 0x5140);  // bytes 0, 1
+    o[1] = sub_h2(h2_pair<1>(mh), 0x64806480u);  // byte 5 of u
+    o[2] = sub_h2(h2_pair<0>(mh), 0x64806480u);  // byte 4
+    o[3] = sub_h2(h2_pair<1>(m1), 0x64806480u);
+    o[4] = sub_h2(h2_pair<0>(m1), 0x64806480u);
+    o[5] = sub_h2(h2_pair<1>(m0), 0x64806480u);
+    o[6] = sub_h2(h2_pair<0>(m0), 0x64806480u);
 }
+
+// Level pair (2q, 2q + 1) of one output: 256 z_2q + z_2q+1 + 0x8B400000 from
+// the magic-constant bits w = 0x4B400000 + z (257 * 0x4B400000 = 0x8B400000
+// mod 2^32); for |z| <= 2^22 the sum lies in [0, 2^32), so it needs no
+// further offset before it is widened.
+__device__ __forceinline__ unsigned level_pair(uint32_t a, uint32_t b) {
+    const unsigned w0 = __float_as_uint(__uint_as_float(a) + 12582912.0f);
+    const unsigned w1 = __float_as_uint(__uint_as_float(b) + 12582912.0f);
+    unsigned d;
+    asm("mad.lo.u32 %0, %1, 256, %2;\n" : "=r"(d) : "r"(w0), "r"(w1));
+    return d;
+}
+
+// Level 6 of one output rounded to the output's unit: 0x4B400000 +
+// floor((z + 128) / 256), one add and one multiply-add rounded down.
+__device__ __forceinline__ unsigned level6(uint32_t a) {
+    return __float_as_uint(__fmaf_rd(__uint_as_float(a) + 128.0f, 0.00390625f, 12582912.0f));
+}
+
+// 2^64 minus the offsets the three pairs (0x8B400000 each, at 2^32, 2^16 and
+// 1) and level 6 (0x4B400000) carry.
+constexpr unsigned kPairOffset = 257u * kMagicBits;  // 0x8B400000 (mod 2^32)
+constexpr unsigned long long kLevelBias =
+    0ull - (unsigned long long)kPairOffset * ((1ull << 32) + (1ull << 16) + 1ull) - kMagicBits;
+static_assert(kPairOffset == 0x8B400000u && kLevelBias == 0x74BF74BF29800000ull, "level offsets");
 
 struct Ctx {
     unsigned char* b;  // block digits / parts in shared memory
@@ -877,33 +918,34 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
         fence_after();
         if (mt_t >= n_mt_of(r0)) return;  // warp-uniform
         const uint32_t t0 = cx.tmem + lane_bits + mt_t * 128 + 8 * cg;
-        constexpr unsigned kPairBias = 0u - 257u * kMagicBits;
-        int P[3][8];
+        // out = P0 2^32 + P1 2^16 + P2 + level 6 (mod 2^64), the offsets removed by one constant
+        unsigned long long y[8];
         uint32_t a[8], b[8];
+        ld8(t0, a);
+        ld8(t0 + R, b);
+        ld_wait();
 #pragma unroll
-        for (int q = 0; q < 3; q++) {
-            ld8(t0 + (2 * q) * R, a);
-            ld8(t0 + (2 * q + 1) * R, b);
-            ld_wait();
+        for (int e = 0; e < 8; e++)
+            y[e] = ((unsigned long long)(level_pair(a[e], b[e]) + (unsigned)(kLevelBias >> 32)) << 32) |
+                   (unsigned)kLevelBias;
+        ld8(t0 + 2 * R, a);
+        ld8(t0 + 3 * R, b);
+        ld_wait();
 #pragma unroll
-            for (int e = 0; e < 8; e++) {
-                const unsigned w0 = __float_as_uint(__uint_as_float(a[e]) + 12582912.0f);
-                const unsigned w1 = __float_as_uint(__uint_as_float(b[e]) + 12582912.0f);
-                P[q][e] = (int)(w0 * 256u + w1 + kPairBias);
-            }
-        }
+        for (int e = 0; e < 8; e++) y[e] = mad_wide(level_pair(a[e], b[e]), 65536u, y[e]);
+        ld8(t0 + 4 * R, a);
+        ld8(t0 + 5 * R, b);
+        ld_wait();
+#pragma unroll
+        for (int e = 0; e < 8; e++) y[e] = mad_wide(level_pair(a[e], b[e]), 1u, y[e]);
         ld8(t0 + 6 * R, a);
         ld_wait();
+#pragma unroll
+        for (int e = 0; e < 8; e++) y[e] = mad_wide(level6(a[e]), 1u, y[e]);
         if (r0 + loc < ng) {
             const int bg = swz<double>(insert_zero_bits<K>(r0, pos)) ^ loc_sw;
-            auto out = [&](int e) {
-                const int t6 = (int)(__float_as_uint(__uint_as_float(a[e]) + 12582912.0f) - kMagicBits + 128u) >> 8;
-                return (long long)(((unsigned long long)(long long)P[0][e] << 32) +
-                                   ((unsigned long long)(long long)P[1][e] << 16) +
-                                   (unsigned long long)(long long)(P[2][e] + t6));
-            };
 #pragma unroll
-            for (int e = 0; e < 4; e++) sm[bg ^ off[e]] = Q2{out(e), out(e + 4)};
+            for (int e = 0; e < 4; e++) sm[bg ^ off[e]] = Q2{(long long)y[e], (long long)y[e + 4]};
         }
     };
     auto issue = [&](int g0, int ab) {
