@@ -467,6 +467,11 @@ void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE, bool inj
         dp.n_ops = (int32_t)(L.ops.size() - dp.op0);
         L.passes.push_back(dp);
     }
+    if (t05 && !c64) {  // complex128 digits: the state stays in Q56 between the circuit's passes
+        const size_t np = L.passes.size();
+        for (size_t i = 0; i < np; i++)
+            L.passes[i].io = (i > 0 ? svk::IO_LOAD_Q56 : 0) | (i + 1 < np ? svk::IO_STORE_Q56 : 0);
+    }
 }
 
 cudaError_t ensure(void** p, size_t* cap, size_t need, bool pinned) {

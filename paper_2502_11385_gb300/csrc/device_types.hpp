@@ -22,11 +22,18 @@ struct alignas(16) DevOp {
     int32_t pad[2];
 };
 
+// How a complex128 tcgen05 pass reads and writes the state: between the
+// passes of one circuit the state stays in the kernel's Q56 fixed point
+// (two int64 per amplitude, the same 16 bytes), so only the first pass
+// converts from float64 and only the last converts back.
+enum PassIo : int32_t { IO_LOAD_Q56 = 1, IO_STORE_Q56 = 2 };
+
 // One tile pass: the tile holds the qubits L[0..m) (ascending, L[j] = j for
 // j < c), the other n - m qubits NL[] index the tiles.
 struct DevPass {
     int32_t n, m, c, n_ops;
     int32_t op0, kmax;    // first op; largest dense block of the pass
+    int32_t io, pad;      // PassIo bits (0: float64 in and out)
     uint64_t tile_count;  // 2^(n-m)
     int8_t L[kMaxQ];
     int8_t NL[kMaxQ];

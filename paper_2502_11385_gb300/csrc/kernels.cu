@@ -1408,19 +1408,25 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
             // loads in flight per thread before the conversions
             constexpr int U = MODE == MODE_T05 ? 8 : 4;
             const int N = 1 << m, nt = blockDim.x;
-            for (int j0 = threadIdx.x; j0 < N; j0 += U * nt) {
-                Cx<double> a[U];
+            auto load = [&](auto conv) {
+                for (int j0 = threadIdx.x; j0 < N; j0 += U * nt) {
+                    Cx<double> a[U];
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int j = j0 + u * nt, r = j >> c;
-                    if (j < N) a[u] = st[base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)];
-                }
+                    for (int u = 0; u < U; u++) {
+                        const int j = j0 + u * nt, r = j >> c;
+                        if (j < N) a[u] = st[base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)];
+                    }
 #pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int j = j0 + u * nt;
-                    if (j < N) sm[swz<double>(j)] = Q2{d2q<kTileFB>(a[u].re), d2q<kTileFB>(a[u].im)};
+                    for (int u = 0; u < U; u++) {
+                        const int j = j0 + u * nt;
+                        if (j < N) sm[swz<double>(j)] = Q2{conv(a[u].re), conv(a[u].im)};
+                    }
                 }
-            }
+            };
+            if (MODE == MODE_T05 && (P.io & IO_LOAD_Q56))  // uniform: the previous pass left Q56
+                load([](double v) { return (long long)__double_as_longlong(v); });
+            else
+                load([](double v) { return d2q<kTileFB>(v); });
         } else {
             constexpr int PER = 16 / sizeof(Store);  // amplitudes per 16-byte vector
             // loads in flight per thread before the shared-memory stores (the
@@ -1495,12 +1501,18 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         } else if constexpr (MODE == MODE_TC || MODE == MODE_T05) {
             constexpr int kTileFB = MODE == MODE_T05 ? 56 : 62;
             const int N = 1 << m;
-            for (int j = threadIdx.x; j < N; j += blockDim.x) {
-                const int r = j >> c;
-                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
-                const Q2 v = sm[swz<double>(j)];
-                st[gidx] = Cx<double>{q2d<kTileFB>(v.re), q2d<kTileFB>(v.im)};
-            }
+            auto store = [&](auto conv) {
+                for (int j = threadIdx.x; j < N; j += blockDim.x) {
+                    const int r = j >> c;
+                    const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                    const Q2 v = sm[swz<double>(j)];
+                    st[gidx] = Cx<double>{conv(v.re), conv(v.im)};
+                }
+            };
+            if (MODE == MODE_T05 && (P.io & IO_STORE_Q56))  // uniform: the next pass reads Q56
+                store([](long long q) { return __longlong_as_double(q); });
+            else
+                store([](long long q) { return q2d<kTileFB>(q); });
         } else {
             constexpr int PER = 16 / sizeof(Store);
             const int nvec = (1 << m) / PER;
