@@ -889,13 +889,23 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
     for (int e = 0; e < 4; e++) off[e] = swz<double>(group_offset<K>(4 * cg + e, pm));
     const int loc = mt_t * 128 + row;
     const int loc_sw = swz<double>(insert_zero_bits<K>(loc, pos));
+    // insert_zero_bits and swz are linear over XOR and round g0 = r GPR has
+    // no bit in common with loc, so the round's base is loc_sw XOR the
+    // offsets S[b] of the set bits b of r (at most 4 rounds per tile here)
+    int S[3];
+#pragma unroll
+    for (int b = 0; b < 3; b++) S[b] = swz<double>(insert_zero_bits<K>(GPR << b, pos));
+    auto base_of = [&](int g0) {
+        const int r = g0 / GPR;
+        return loc_sw ^ ((r & 1) ? S[0] : 0) ^ ((r & 2) ? S[1] : 0) ^ ((r & 4) ? S[2] : 0);
+    };
     auto n_mt_of = [&](int g0) { return (K == 3 && g0 + 128 < ng) ? 2 : 1; };
     // digits of the thread's 4 amplitudes of the round at g0 into A buffer ab
     auto split = [&](int g0, int ab) {
         if (mt_t >= n_mt_of(g0)) return;  // warp-uniform
         unsigned d[4][7];
         if (g0 + loc < ng) {
-            const int bg = swz<double>(insert_zero_bits<K>(g0, pos)) ^ loc_sw;
+            const int bg = base_of(g0);
             Q2 v[4];
 #pragma unroll
             for (int e = 0; e < 4; e++) v[e] = sm[bg ^ off[e]];
@@ -943,7 +953,7 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
 #pragma unroll
         for (int e = 0; e < 8; e++) y[e] = mad_wide(level6(a[e]), 1u, y[e]);
         if (r0 + loc < ng) {
-            const int bg = swz<double>(insert_zero_bits<K>(r0, pos)) ^ loc_sw;
+            const int bg = base_of(r0);
 #pragma unroll
             for (int e = 0; e < 4; e++) sm[bg ^ off[e]] = Q2{(long long)y[e], (long long)y[e + 4]};
         }
@@ -1099,10 +1109,19 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
 #pragma unroll
     for (int e = 0; e < P; e++) off[e] = swz<float>(group_offset<K>(P * cg + e, pm));
     const int row_sw = swz<float>(insert_zero_bits<K>(row, pos));
+    // round bases from per-op offsets, as in the complex128 digit op (rounds of
+    // 128 groups, at most 16 per tile)
+    int S[4];
+#pragma unroll
+    for (int b = 0; b < 4; b++) S[b] = swz<float>(insert_zero_bits<K>(128 << b, pos));
+    auto base_of = [&](int g0) {
+        const int r = g0 >> 7;
+        return row_sw ^ ((r & 1) ? S[0] : 0) ^ ((r & 2) ? S[1] : 0) ^ ((r & 4) ? S[2] : 0) ^ ((r & 8) ? S[3] : 0);
+    };
     auto split = [&](int g0, int ab) {
         unsigned h[2][P / 2], mm[2][P / 2], l[2][P / 2];
         if (g0 + row < ng) {
-            const int bg = swz<float>(insert_zero_bits<K>(g0, pos)) ^ row_sw;
+            const int bg = base_of(g0);
             Cx<float> v[P];
 #pragma unroll
             for (int e = 0; e < P; e++) v[e] = sm[bg ^ off[e]];
@@ -1143,7 +1162,7 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
         ldN<2 * P>(t0 + 2 * R, z2);
         ld_wait();
         if (r0 + row < ng) {
-            const int bg = swz<float>(insert_zero_bits<K>(r0, pos)) ^ row_sw;
+            const int bg = base_of(r0);
             auto y = [&](int c) {
                 return (__uint_as_float(z2[c]) + __uint_as_float(z1[c])) + __uint_as_float(z0[c]);
             };
