@@ -844,6 +844,42 @@ constexpr unsigned long long kLevelBias =
     0ull - (unsigned long long)kPairOffset * ((1ull << 32) + (1ull << 16) + 1ull) - kMagicBits;
 static_assert(kPairOffset == 0x8B400000u && kLevelBias == 0x74BF74BF29800000ull, "level offsets");
 
+// Per-op address table of a pass (ints, built once per CTA and pass): every
+// tile of the pass applies the same ops, so the swizzled offsets a thread
+// needs depend only on the op's qubit positions.  insert_zero_bits and swz
+// are linear over XOR, so the base of group g splits into its lane bits
+// (kTabLane + (g & 31)), its higher bits (kTabHi + (g >> 5)) and the round
+// (kTabS + b for bit b of the round index).
+constexpr int kTabOff = 0;    // [b] = swz(group_offset(b)), b < 2^k
+constexpr int kTabS = 32;     // [b] = swz(insert_zero_bits(groups_per_round << b))
+constexpr int kTabLane = 36;  // [l] = swz(insert_zero_bits(l)), l < 32
+constexpr int kTabHi = 68;    // [h] = swz(insert_zero_bits(h << 5)), h < 8
+constexpr int kTabInts = 80;
+
+template <typename SwzT>
+__device__ __forceinline__ int op_table_entry(const DevOp& op, int kt, int gpr, int t) {
+    if (op.kind != OP_DENSE) return 0;
+    int pos[5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) pos[j] = j < kt ? op.pos[j] : 0;
+    auto ins = [&](int g) {
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            if (j < kt) g = ((g >> pos[j]) << (pos[j] + 1)) | (g & ((1 << pos[j]) - 1));
+        return g;
+    };
+    if (t < kTabS) {
+        int off = 0;
+#pragma unroll
+        for (int j = 0; j < 5; j++)
+            if (j < kt && ((t >> j) & 1)) off |= 1 << pos[j];
+        return swz<SwzT>(off);
+    }
+    if (t < kTabLane) return swz<SwzT>(ins(gpr << (t - kTabS)));
+    if (t < kTabHi) return swz<SwzT>(ins(t - kTabLane));
+    return swz<SwzT>(ins((t - kTabHi) << 5));
+}
+
 struct Ctx {
     unsigned char* b;  // block digits / parts in shared memory
     uint32_t b_addr, mbar, tmem;
@@ -864,7 +900,8 @@ struct Ctx {
 // While the MMAs of round r run, the threads split round r + 1 into the other
 // A buffer; the (single) accumulator is re-assembled after the MMAs finish.
 template <int K>
-__device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const uint4* __restrict__ Bg, Ctx& cx) {
+__device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const uint4* __restrict__ Bg, Ctx& cx,
+                                         const int* tab) {
     static_assert(K == 3 || K == 4, "tensor-core blocks have 3 or 4 qubits");
     constexpr int D = 1 << K, R = 2 * D;
     constexpr int SBO = 16 * R;              // B: bytes between 8-row core groups
@@ -885,16 +922,28 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
     const int row = (warp & 3) * 32 + lane;
     const uint32_t lane_bits = (uint32_t)((warp & 3) * 32) << 16;
     int off[4];
-#pragma unroll
-    for (int e = 0; e < 4; e++) off[e] = swz<double>(group_offset<K>(4 * cg + e, pm));
     const int loc = mt_t * 128 + row;
-    const int loc_sw = swz<double>(insert_zero_bits<K>(loc, pos));
+    int loc_sw;
     // insert_zero_bits and swz are linear over XOR and round g0 = r GPR has
     // no bit in common with loc, so the round's base is loc_sw XOR the
     // offsets S[b] of the set bits b of r (at most 4 rounds per tile here)
     int S[3];
+    if (tab) {  // the pass's table (shared memory)
+        const int4 o4 = *reinterpret_cast<const int4*>(tab + kTabOff + 4 * cg);
+        off[0] = o4.x;
+        off[1] = o4.y;
+        off[2] = o4.z;
+        off[3] = o4.w;
+        loc_sw = tab[kTabLane + (loc & 31)] ^ tab[kTabHi + (loc >> 5)];
 #pragma unroll
-    for (int b = 0; b < 3; b++) S[b] = swz<double>(insert_zero_bits<K>(GPR << b, pos));
+        for (int b = 0; b < 3; b++) S[b] = tab[kTabS + b];
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; e++) off[e] = swz<double>(group_offset<K>(4 * cg + e, pm));
+        loc_sw = swz<double>(insert_zero_bits<K>(loc, pos));
+#pragma unroll
+        for (int b = 0; b < 3; b++) S[b] = swz<double>(insert_zero_bits<K>(GPR << b, pos));
+    }
     auto base_of = [&](int g0) {
         const int r = g0 / GPR;
         return loc_sw ^ ((r & 1) ? S[0] : 0) ^ ((r & 2) ? S[1] : 0) ^ ((r & 4) ? S[2] : 0);
@@ -1334,6 +1383,7 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
     __shared__ uint32_t t05_tmem;
     constexpr int kOpCache = 48;  // the pass's op descriptors, read once per pass
     __shared__ DevOp s_ops[kOpCache];
+    __shared__ __align__(16) int s_tab[MODE == MODE_T05 ? kOpCache * t05::kTabInts : 4];
     t05::Ctx cx{};
     if constexpr (uses_tmem(MODE)) {
         if (threadIdx.x < 32) {  // warp 0 owns the tensor-memory allocation
@@ -1379,6 +1429,14 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
                 const int4* osrc = reinterpret_cast<const int4*>(ops + P.op0);
                 int4* odst = reinterpret_cast<int4*>(s_ops);
                 for (int i = threadIdx.x; i < P.n_ops * (int)(sizeof(DevOp) / 16); i += blockDim.x) odst[i] = osrc[i];
+                if constexpr (MODE == MODE_T05) {  // the pass's address tables, from the global descriptors
+                    for (int i = threadIdx.x; i < P.n_ops * t05::kTabInts; i += blockDim.x) {
+                        const int o = i / t05::kTabInts;
+                        const DevOp& op = ops[P.op0 + o];
+                        const int kt = op.k <= 3 ? 3 : 4;
+                        s_tab[i] = t05::op_table_entry<double>(op, kt, kt == 3 ? 256 : 128, i - o * t05::kTabInts);
+                    }
+                }
             }
             if (threadIdx.x < 64) {
                 const int w = threadIdx.x >> 5, v = threadIdx.x & 31, hb = P.m - P.c;
@@ -1490,8 +1548,11 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
             if constexpr (MODE == MODE_T05) {
                 if (op.kind == OP_DIAG)
                     op_diag_tc<t05::kLogThreads>(sm, m, op, reinterpret_cast<const Q2*>(coef + op.coeff), base);
-                else if (op.k <= 3) t05::op_dense<3>(sm, m, op, coef + op.coeff, cx);
-                else t05::op_dense<(KMAX >= 4 ? 4 : 3)>(sm, m, op, coef + op.coeff, cx);  // capped at 4 qubits
+                else {
+                    const int* tab = n_ops <= kOpCache ? s_tab + o * t05::kTabInts : nullptr;
+                    if (op.k <= 3) t05::op_dense<3>(sm, m, op, coef + op.coeff, cx, tab);
+                    else t05::op_dense<(KMAX >= 4 ? 4 : 3)>(sm, m, op, coef + op.coeff, cx, tab);  // capped at 4 qubits
+                }
                 if (cx.failed) break;  // uniform: decided by a block-wide vote
             } else if constexpr (MODE == MODE_T32) {
                 if (op.kind == OP_DIAG)

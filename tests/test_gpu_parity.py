@@ -418,8 +418,14 @@ def _tc_arith(sv, mode):
 
 @pytest.mark.parametrize("mode", TC_MODES)
 def test_tc_brickwork12(sv, mode):
+    """Unfused, the 175 blocks share one pass, past the kernel's 48-op cache
+    (the op computes its own address table); fused, the pass's tables are
+    built once per CTA."""
     g = W.workload_brickwork12()
     ref = oracle.run(12, g)
+    opts = sv.run_opts(max_fuse_k=1, arith=_tc_arith(sv, mode))
+    assert max(len(sv.Plan(12, "c128", g, opts).pass_info(i)["blocks"])
+               for i in range(sv.Plan(12, "c128", g, opts).summary()["n_passes"])) > 48
     for k in (1, 3, 4, 5):
         st = _check(sv, 12, "c128", g, ref, max_fuse_k=k, arith=_tc_arith(sv, mode))
         assert st["arith"] == _tc_arith(sv, mode)
