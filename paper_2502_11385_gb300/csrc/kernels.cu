@@ -1135,7 +1135,7 @@ __device__ __forceinline__ void ldN<16>(uint32_t taddr, uint32_t (&r)[16]) {
 // A buffer; the accumulator is re-assembled after the MMAs finish.
 template <int K>
 __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, const uint4* __restrict__ Bg,
-                                         t05::Ctx& cx) {
+                                         t05::Ctx& cx, const int* tab) {
     static_assert(K >= 3 && K <= 5, "tensor-core blocks have 3 to 5 qubits");
     using namespace t05;
     constexpr int D = 1 << K, R = 2 * D;
@@ -1155,14 +1155,23 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
     const int row = (warp & 3) * 32 + lane;
     const uint32_t lane_bits = (uint32_t)((warp & 3) * 32) << 16;
     int off[P];
-#pragma unroll
-    for (int e = 0; e < P; e++) off[e] = swz<float>(group_offset<K>(P * cg + e, pm));
-    const int row_sw = swz<float>(insert_zero_bits<K>(row, pos));
+    int row_sw;
     // round bases from per-op offsets, as in the complex128 digit op (rounds of
     // 128 groups, at most 16 per tile)
     int S[4];
+    if (tab) {  // the pass's table (shared memory)
 #pragma unroll
-    for (int b = 0; b < 4; b++) S[b] = swz<float>(insert_zero_bits<K>(128 << b, pos));
+        for (int e = 0; e < P; e++) off[e] = tab[kTabOff + P * cg + e];
+        row_sw = tab[kTabLane + lane] ^ tab[kTabHi + (warp & 3)];
+#pragma unroll
+        for (int b = 0; b < 4; b++) S[b] = tab[kTabS + b];
+    } else {
+#pragma unroll
+        for (int e = 0; e < P; e++) off[e] = swz<float>(group_offset<K>(P * cg + e, pm));
+        row_sw = swz<float>(insert_zero_bits<K>(row, pos));
+#pragma unroll
+        for (int b = 0; b < 4; b++) S[b] = swz<float>(insert_zero_bits<K>(128 << b, pos));
+    }
     auto base_of = [&](int g0) {
         const int r = g0 >> 7;
         return row_sw ^ ((r & 1) ? S[0] : 0) ^ ((r & 2) ? S[1] : 0) ^ ((r & 4) ? S[2] : 0) ^ ((r & 8) ? S[3] : 0);
@@ -1383,7 +1392,7 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
     __shared__ uint32_t t05_tmem;
     constexpr int kOpCache = 48;  // the pass's op descriptors, read once per pass
     __shared__ DevOp s_ops[kOpCache];
-    __shared__ __align__(16) int s_tab[MODE == MODE_T05 ? kOpCache * t05::kTabInts : 4];
+    __shared__ __align__(16) int s_tab[uses_tmem(MODE) ? kOpCache * t05::kTabInts : 4];
     t05::Ctx cx{};
     if constexpr (uses_tmem(MODE)) {
         if (threadIdx.x < 32) {  // warp 0 owns the tensor-memory allocation
@@ -1429,12 +1438,18 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
                 const int4* osrc = reinterpret_cast<const int4*>(ops + P.op0);
                 int4* odst = reinterpret_cast<int4*>(s_ops);
                 for (int i = threadIdx.x; i < P.n_ops * (int)(sizeof(DevOp) / 16); i += blockDim.x) odst[i] = osrc[i];
-                if constexpr (MODE == MODE_T05) {  // the pass's address tables, from the global descriptors
+                if constexpr (uses_tmem(MODE)) {  // the pass's address tables, from the global descriptors
                     for (int i = threadIdx.x; i < P.n_ops * t05::kTabInts; i += blockDim.x) {
-                        const int o = i / t05::kTabInts;
+                        const int o = i / t05::kTabInts, t = i - o * t05::kTabInts;
                         const DevOp& op = ops[P.op0 + o];
-                        const int kt = op.k <= 3 ? 3 : 4;
-                        s_tab[i] = t05::op_table_entry<double>(op, kt, kt == 3 ? 256 : 128, i - o * t05::kTabInts);
+                        // the block size each op is dispatched with below
+                        if constexpr (MODE == MODE_T05) {
+                            const int kt = op.k <= 3 ? 3 : (KMAX >= 4 ? 4 : 3);
+                            s_tab[i] = t05::op_table_entry<double>(op, kt, kt == 3 ? 256 : 128, t);
+                        } else {
+                            const int kt = op.k <= 3 ? 3 : (op.k == 4 ? (KMAX >= 4 ? 4 : 3) : (KMAX >= 5 ? 5 : 3));
+                            s_tab[i] = t05::op_table_entry<float>(op, kt, 128, t);
+                        }
                     }
                 }
             }
@@ -1558,9 +1573,12 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
                 if (op.kind == OP_DIAG)
                     op_diag<float, t05::kLogThreads>(sm, m, op, reinterpret_cast<const Cx<float>*>(coef + op.coeff),
                                                      base);
-                else if (op.k <= 3) t32::op_dense<3>(sm, m, op, coef + op.coeff, cx);  // smaller blocks are padded
-                else if (op.k == 4) t32::op_dense<(KMAX >= 4 ? 4 : 3)>(sm, m, op, coef + op.coeff, cx);
-                else t32::op_dense<(KMAX >= 5 ? 5 : 3)>(sm, m, op, coef + op.coeff, cx);
+                else {
+                    const int* tab = n_ops <= kOpCache ? s_tab + o * t05::kTabInts : nullptr;
+                    if (op.k <= 3) t32::op_dense<3>(sm, m, op, coef + op.coeff, cx, tab);  // smaller blocks are padded
+                    else if (op.k == 4) t32::op_dense<(KMAX >= 4 ? 4 : 3)>(sm, m, op, coef + op.coeff, cx, tab);
+                    else t32::op_dense<(KMAX >= 5 ? 5 : 3)>(sm, m, op, coef + op.coeff, cx, tab);
+                }
                 if (cx.failed) break;
             } else {
                 apply_op<MODE, KMAX>(sm, m, op, coef + op.coeff, base);
