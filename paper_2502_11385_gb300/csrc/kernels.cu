@@ -1515,10 +1515,19 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
                     }
                 }
             };
-            if (MODE == MODE_T05 && (P.io & IO_LOAD_Q56))  // uniform: the previous pass left Q56
-                load([](double v) { return (long long)__double_as_longlong(v); });
-            else
+            if (MODE == MODE_T05 && (P.io & IO_LOAD_Q56)) {
+                // uniform: the previous pass left Q56, a plain copy: every 16-byte
+                // slot of the tile in flight at once, global to shared memory
+                const uint32_t sbase = t05::smem_addr(sm);
+                for (int j = threadIdx.x; j < N; j += nt) {
+                    const int r = j >> c;
+                    t05::cp_async16(sbase + 16u * (uint32_t)swz<double>(j),
+                                    st + (base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)));
+                }
+                t05::cp_async_wait_all();
+            } else {
                 load([](double v) { return d2q<kTileFB>(v); });
+            }
         } else {
             constexpr int PER = 16 / sizeof(Store);  // amplitudes per 16-byte vector
             // loads in flight per thread before the shared-memory stores (the
