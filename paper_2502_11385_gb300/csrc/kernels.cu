@@ -1530,23 +1530,22 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
             }
         } else {
             constexpr int PER = 16 / sizeof(Store);  // amplitudes per 16-byte vector
-            // loads in flight per thread before the shared-memory stores (the
-            // one-CTA-per-SM tensor-memory mode has no other CTA to hide them)
-            constexpr int U = uses_tmem(MODE) ? 8 : 1;
+            // the one-CTA-per-SM tensor-memory mode has no other CTA to hide
+            // the loads: it copies with cp.async, the whole tile in flight
             const int nvec = (1 << m) / PER, nt = blockDim.x;
-            for (int v0 = threadIdx.x; v0 < nvec; v0 += U * nt) {
-                int4 a[U];
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int v = v0 + u * nt, j = v * PER, r = j >> c;
-                    if (v < nvec)
-                        a[u] = *reinterpret_cast<const int4*>(
-                            st + (base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)));
+            if constexpr (uses_tmem(MODE)) {
+                const uint32_t sbase = t05::smem_addr(sm);
+                for (int v = threadIdx.x; v < nvec; v += nt) {
+                    const int j = v * PER, r = j >> c;
+                    t05::cp_async16(sbase + (uint32_t)(sizeof(Smem) * swz<SwzT>(j)),
+                                    st + (base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)));
                 }
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int v = v0 + u * nt;
-                    if (v < nvec) *reinterpret_cast<int4*>(sm + swz<SwzT>(v * PER)) = a[u];
+                t05::cp_async_wait_all();
+            } else {
+                for (int v = threadIdx.x; v < nvec; v += nt) {
+                    const int j = v * PER, r = j >> c;
+                    *reinterpret_cast<int4*>(sm + swz<SwzT>(j)) = *reinterpret_cast<const int4*>(
+                        st + (base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)));
                 }
             }
         }
