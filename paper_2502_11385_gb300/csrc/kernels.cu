@@ -699,6 +699,17 @@ constexpr int kSmemBase = kBBytes;  // block digits; the amplitude tile follows 
 constexpr int kSmemMin = 116 * 1024;       // one CTA per SM (it holds all 512 TMEM columns)
 constexpr int kTmemCols = 512;             // the whole of an SM's tensor memory
 constexpr unsigned kMagicBits = 0x4B400000u;  // bits of 1.5 * 2^23
+// The accumulator starts every round at 1.5 * 2^23 = 3072 * 4096: one MMA of
+// a constant A slice (TMEM columns kAConst.., K-element 0 = fp16 3072, the
+// rest 0; free columns beside both A buffers) by a constant B slice (shared
+// memory, K-row 0 = fp16 4096), so every level sum z lands as the float
+// 1.5 * 2^23 + z, whose bits are 0x4B400000 + z: the level is read as an
+// integer without a float add.  The host's per-block bound |z| <= 2^22
+// holds for every partial sum too (it bounds the sum of the products'
+// magnitudes), so each partial sum stays an integer in [2^23, 2^24].
+constexpr uint32_t kAConst = 368;
+constexpr unsigned kHalf3072 = 0x6A00u, kHalf4096 = 0x6C00u;
+constexpr int kBiasRows = 7 * 32;  // N of the widest accumulator (7 R, R = 32)
 constexpr unsigned long long kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
 constexpr unsigned kWaitPolls = 1u << 26;                 // and after this many polls in any case
 
@@ -820,21 +831,20 @@ __device__ __forceinline__ void bal_digits_pair(long long x0, long long x1, unsi
 }
 
 // Level pair (2q, 2q + 1) of one output: 256 z_2q + z_2q+1 + 0x8B400000 from
-// the magic-constant bits w = 0x4B400000 + z (257 * 0x4B400000 = 0x8B400000
+// the accumulator bits w = 0x4B400000 + z (257 * 0x4B400000 = 0x8B400000
 // mod 2^32); for |z| <= 2^22 the sum lies in [0, 2^32), so it needs no
 // further offset before it is widened.
-__device__ __forceinline__ unsigned level_pair(uint32_t a, uint32_t b) {
-    const unsigned w0 = __float_as_uint(__uint_as_float(a) + 12582912.0f);
-    const unsigned w1 = __float_as_uint(__uint_as_float(b) + 12582912.0f);
+__device__ __forceinline__ unsigned level_pair(uint32_t w0, uint32_t w1) {
     unsigned d;
     asm("mad.lo.u32 %0, %1, 256, %2;\n" : "=r"(d) : "r"(w0), "r"(w1));
     return d;
 }
 
 // Level 6 of one output rounded to the output's unit: 0x4B400000 +
-// floor((z + 128) / 256), one add and one multiply-add rounded down.
+// floor((z + 128) / 256) from the accumulator 1.5 * 2^23 + z: one exact add
+// (z + 128) and one multiply-add rounded down.
 __device__ __forceinline__ unsigned level6(uint32_t a) {
-    return __float_as_uint(__fmaf_rd(__uint_as_float(a) + 128.0f, 0.00390625f, 12582912.0f));
+    return __float_as_uint(__fmaf_rd(__uint_as_float(a) + (128.0f - 12582912.0f), 0.00390625f, 12582912.0f));
 }
 
 // 2^64 minus the offsets the three pairs (0x8B400000 each, at 2^32, 2^16 and
@@ -883,6 +893,7 @@ __device__ __forceinline__ int op_table_entry(const DevOp& op, int kt, int gpr, 
 struct Ctx {
     unsigned char* b;  // block digits / parts in shared memory
     uint32_t b_addr, mbar, tmem;
+    uint32_t bias_addr;  // complex128 digits: the constant B slice of the accumulator preload
     uint32_t phase;
     bool failed;
 };
@@ -1012,7 +1023,13 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
         if (tid != 0 || (op.flags & OPF_TEST_NO_MMA)) return;
         fence_after();
         const int n_mt = n_mt_of(g0);
-        for (int mt = 0; mt < n_mt; mt++)
+        for (int mt = 0; mt < n_mt; mt++) {
+            // accumulator <- 1.5 * 2^23 in all 7R columns, then every digit MMA accumulates
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(cx.tmem + mt * 128),
+                "r"(cx.tmem + kAConst), "l"(desc(cx.bias_addr, 128, 256)), "r"(idesc(7 * R)), "r"(0u)
+                : "memory");
 #pragma unroll
             for (int i = 0; i < 7; i++)
 #pragma unroll
@@ -1023,9 +1040,10 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
                         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                         "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(
                             cx.tmem + mt * 128 + i * R),
-                        "r"(ta), "l"(db), "r"(idesc((7 - i) * R)), "r"((uint32_t)((i | ks) != 0))
+                        "r"(ta), "l"(db), "r"(idesc((7 - i) * R)), "r"(1u)
                         : "memory");
                 }
+        }
         commit(cx.mbar);
     };
     split(0, 0);
@@ -1393,6 +1411,9 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
     constexpr int kOpCache = 48;  // the pass's op descriptors, read once per pass
     __shared__ DevOp s_ops[kOpCache];
     __shared__ __align__(16) int s_tab[uses_tmem(MODE) ? kOpCache * t05::kTabInts : 4];
+    // complex128 digits: the constant B slice of the accumulator preload (7R x 16 fp16, K-major
+    // core matrices: 8-row groups 256 bytes apart, the two 8-element K halves 128 bytes apart)
+    __shared__ __align__(128) unsigned s_bias_b[MODE == MODE_T05 ? t05::kBiasRows * 8 : 1];
     t05::Ctx cx{};
     if constexpr (uses_tmem(MODE)) {
         if (threadIdx.x < 32) {  // warp 0 owns the tensor-memory allocation
@@ -1413,8 +1434,25 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         cx.b_addr = t05::smem_addr(cx.b);
         cx.mbar = t05::smem_addr(&t05_mbar);
         cx.tmem = t05_tmem;
+        cx.bias_addr = t05::smem_addr(s_bias_b);
         cx.phase = 0;
         cx.failed = false;
+        if constexpr (MODE == MODE_T05) {
+            // K-element 0 of every row: B = 4096 (first word of each 16-byte row of the low K half)
+            for (int w = threadIdx.x; w < t05::kBiasRows * 8; w += blockDim.x)
+                s_bias_b[w] = ((w & 3) == 0 && (w & 63) < 32) ? t05::kHalf4096 : 0u;
+            if (threadIdx.x < 128) {  // A = 3072 at K-element 0 of every TMEM lane, one lane quarter per warp
+                const uint32_t ta = t05_tmem + ((uint32_t)(threadIdx.x & ~31) << 16) + t05::kAConst;
+                asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%2,%2,%2,%2,%2,%2};\n" ::"r"(ta),
+                             "r"(t05::kHalf3072), "r"(0u)
+                             : "memory");
+                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+            }
+            t05::fence_async_smem();
+            t05::fence_before();
+            __syncthreads();
+            t05::fence_after();
+        }
     }
     int cur = -1;
     for (uint64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
