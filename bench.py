@@ -130,11 +130,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def code_of(text):
+    """C/C++ source without comments and whitespace (string literals kept)."""
+    import re
+    pat = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)
+    text = pat.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text)
+    return "".join(text.split())
+
+
 def kernel_hash():
+    """Hash of the kernel code (comments and whitespace ignored), recorded
+    beside each ncu traffic figure so that a figure is used only for the code
+    it was taken from."""
     h = hashlib.sha256()
     for f in ("kernels.cu", "device_types.hpp"):
-        with open(os.path.join(ROOT, "paper_2502_11385_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2502_11385_gb300", "csrc", f)) as fh:
+            h.update(code_of(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

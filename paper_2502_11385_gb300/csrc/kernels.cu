@@ -668,9 +668,10 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
 // place two such values b in the mantissas of 1024 + b, one packed half
 // subtraction removes 1024 + 128 (1024 + 256 for X_0).  For a unitary block
 // every level sum then stays below 2^21.5 (the host checks the bound 2^22 per
-// block), so a level becomes an integer with one float add: the bits of
-// z + 1.5 * 2^23 are 0x4B400000 + z.  The digit work is bound by the SM's
-// integer pipe, so the re-assembly keeps to float adds and multiply-adds.
+// block), so it is exact in float32, and with the accumulator started at
+// 1.5 * 2^23 (below) its bits are 0x4B400000 + z: the level reads as an
+// integer.  The digit work is bound by the SM's integer pipe, so the
+// re-assembly keeps to multiply-adds.
 //
 // One round covers 128 groups (one M = 128 tile; 3-qubit blocks take two
 // M-tiles per round):
