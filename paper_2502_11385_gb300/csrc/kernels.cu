@@ -1456,6 +1456,9 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         }
     }
     int cur = -1;
+    // tensor-memory modes: this tile's cp.async loads were issued during the
+    // previous tile's store phase (same entry, Q56 / float32 in HBM)
+    bool preloaded = false;
     for (uint64_t t = blockIdx.x; t < total_tiles; t += gridDim.x) {
         int lo = 0, hi = n_entries - 1;  // entry owning tile t (uniform across the CTA)
         while (lo < hi) {
@@ -1554,7 +1557,9 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
                     }
                 }
             };
-            if (MODE == MODE_T05 && (P.io & IO_LOAD_Q56)) {
+            if (MODE == MODE_T05 && preloaded) {
+                t05::cp_async_wait_all();
+            } else if (MODE == MODE_T05 && (P.io & IO_LOAD_Q56)) {
                 // uniform: the previous pass left Q56, a plain copy: every 16-byte
                 // slot of the tile in flight at once, global to shared memory
                 const uint32_t sbase = t05::smem_addr(sm);
@@ -1573,11 +1578,13 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
             // the loads: it copies with cp.async, the whole tile in flight
             const int nvec = (1 << m) / PER, nt = blockDim.x;
             if constexpr (uses_tmem(MODE)) {
-                const uint32_t sbase = t05::smem_addr(sm);
-                for (int v = threadIdx.x; v < nvec; v += nt) {
-                    const int j = v * PER, r = j >> c;
-                    t05::cp_async16(sbase + (uint32_t)(sizeof(Smem) * swz<SwzT>(j)),
-                                    st + (base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)));
+                if (!preloaded) {
+                    const uint32_t sbase = t05::smem_addr(sm);
+                    for (int v = threadIdx.x; v < nvec; v += nt) {
+                        const int j = v * PER, r = j >> c;
+                        t05::cp_async16(sbase + (uint32_t)(sizeof(Smem) * swz<SwzT>(j)),
+                                        st + (base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask)));
+                    }
                 }
                 t05::cp_async_wait_all();
             } else {
@@ -1646,14 +1653,21 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         } else if constexpr (MODE == MODE_TC || MODE == MODE_T05) {
             constexpr int kTileFB = MODE == MODE_T05 ? 56 : 62;
             const int N = 1 << m;
+            // the CTA's next tile (same entry) reads Q56: each thread refills its
+            // slots with it by cp.async as soon as it has stored them
+            const uint64_t bn = s_next_base;
+            const bool fuse = MODE == MODE_T05 && bn != ~0ull && (P.io & IO_LOAD_Q56);
+            const uint32_t sbase = t05::smem_addr(sm);
             auto store = [&](auto conv) {
                 for (int j = threadIdx.x; j < N; j += blockDim.x) {
                     const int r = j >> c;
-                    const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                    const uint64_t dj = dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
                     const Q2 v = sm[swz<double>(j)];
-                    st[gidx] = Cx<double>{conv(v.re), conv(v.im)};
+                    st[base | dj] = Cx<double>{conv(v.re), conv(v.im)};
+                    if (fuse) t05::cp_async16(sbase + 16u * (uint32_t)swz<double>(j), st + (bn | dj));
                 }
             };
+            preloaded = fuse;
             if (MODE == MODE_T05 && (P.io & IO_STORE_Q56))  // uniform: the next pass reads Q56
                 store([](long long q) { return __longlong_as_double(q); });
             else
@@ -1661,12 +1675,18 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
         } else {
             constexpr int PER = 16 / sizeof(Store);
             const int nvec = (1 << m) / PER;
+            // tensor-memory mode: refill each stored slot with the CTA's next tile (same entry) by cp.async
+            const uint64_t bn = s_next_base;
+            const bool fuse = uses_tmem(MODE) && bn != ~0ull;
+            const uint32_t sbase = t05::smem_addr(sm);
             for (int v = threadIdx.x; v < nvec; v += blockDim.x) {
                 const int j = v * PER;
                 const int r = j >> c;
-                const uint64_t gidx = base | dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
-                *reinterpret_cast<int4*>(st + gidx) = *reinterpret_cast<const int4*>(sm + swz<SwzT>(j));
+                const uint64_t dj = dep[0][r & 31] | dep[1][(r >> 5) & 31] | (uint64_t)(j & cmask);
+                *reinterpret_cast<int4*>(st + (base | dj)) = *reinterpret_cast<const int4*>(sm + swz<SwzT>(j));
+                if (fuse) t05::cp_async16(sbase + (uint32_t)(sizeof(Smem) * swz<SwzT>(j)), st + (bn | dj));
             }
+            preloaded = fuse;
         }
         __syncthreads();
     }
