@@ -84,7 +84,7 @@ typedef struct {
  *   SV_ARITH_TC_SYNC: the same digit products on the warp-level mma.sync
  *                    path (unsigned lower digits), kept as the measured
  *                    baseline of the tensor-memory kernel.
- *   SV_ARITH_AUTO:   SV_ARITH_TC for states of 19 or more qubits, else
+ *   SV_ARITH_AUTO:   SV_ARITH_TC for states of 20 or more qubits, else
  *                    SV_ARITH_DF64 (measured crossover; on GB300 the FP64
  *                    pipe runs at about 1/70 of the FP32 pipe, so native
  *                    FP64 is never the automatic choice).  SV_ARITH_TC and

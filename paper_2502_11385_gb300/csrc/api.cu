@@ -115,12 +115,14 @@ int max_tile(int dt, const svk::DevInfo& di) {
 
 // complex128 arithmetic.  SV_ARITH_AUTO takes the tensor-memory digit mode
 // from kAutoTcQubits qubits on (measured crossover on GB300: below it the
-// state is a handful of tiles and the double-float pass, with less work per
-// op, is faster) and double-float arithmetic below; explicit tensor-core
-// modes need tiles of at least 8 qubits and fall back to double-float below.
-constexpr int kAutoTcQubits = 19;
+// state is at most 64 tiles, fewer than the SMs, and the double-float pass,
+// with less work per op, is faster: 19 q 1.50 ms vs 1.90 ms per circuit,
+// 20 q 2.46 ms vs 2.00 ms) and double-float arithmetic below; explicit
+// tensor-core modes need tiles of at least 8 qubits and fall back to
+// double-float below.
+constexpr int kAutoTcQubits = 20;
 // complex64: the float32 FMA pass wins up to 22 qubits (measured: 22 q
-// 2.66 ms vs 2.78 ms per circuit, 24 q 8.97 ms vs 5.71 ms)
+// 2.52 ms vs 2.71 ms per circuit, 23 q 4.26 ms vs 3.40 ms)
 constexpr int kAutoTc32Qubits = 23;
 
 int resolve_arith(int dt, const sv_run_opts* o, int n = 34) {

@@ -514,10 +514,10 @@ def test_auto_arith_falls_back_for_unnormalised_amplitudes(sv):
 
 
 def test_auto_arith_threshold(sv):
-    """SV_ARITH_AUTO: complex128 below 19 qubits in double-float, tcgen05
-    digits from 19 on; complex64 below 23 qubits in float32 FMAs, tcgen05
+    """SV_ARITH_AUTO: complex128 below 20 qubits in double-float, tcgen05
+    digits from 20 on; complex64 below 23 qubits in float32 FMAs, tcgen05
     triple split from 23 on."""
-    for n, want in ((18, sv.ARITH_DF64), (19, sv.ARITH_TC)):
+    for n, want in ((19, sv.ARITH_DF64), (20, sv.ARITH_TC)):
         g = _random_circuit(n, 40, 700 + n)
         st = _check(sv, n, "c128", g)
         assert st["arith"] == want, (n, st["arith"])
