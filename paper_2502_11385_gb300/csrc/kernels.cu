@@ -693,8 +693,10 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
 // ---------------------------------------------------------------------------
 namespace t05 {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 512;              // split / re-assembly threads: 16 warps, 4 per TMEM lane quarter
 constexpr int kLogThreads = 9;
+constexpr int kCtaThreads = kThreads + 32; // complex64 mode: plus one warp that only issues the MMAs
+constexpr int kIssuer = kThreads;          // its first thread
 constexpr int kBBytes = 14 * 32 * 32;      // 7R x R fp16 for R = 32
 constexpr int kSmemBase = kBBytes;  // block digits; the amplitude tile follows (A lives in tensor memory)
 constexpr int kSmemMin = 116 * 1024;       // one CTA per SM (it holds all 512 TMEM columns)
@@ -1168,9 +1170,10 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
         pm[j] = 1 << pos[j];
     }
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int i = tid; i < 6 * R * R / 16; i += kThreads) cp_async16(cx.b_addr + 16 * i, Bg + i);
+    const bool worker = tid < kThreads;  // warp-uniform; the last warp only issues the MMAs
+    for (int i = tid; i < 6 * R * R / 16; i += kCtaThreads) cp_async16(cx.b_addr + 16 * i, Bg + i);
     const int ng = 1 << (m - K);
-    const int cg = warp >> 2;
+    const int cg = (warp & 15) >> 2;
     const int row = (warp & 3) * 32 + lane;
     const uint32_t lane_bits = (uint32_t)((warp & 3) * 32) << 16;
     int off[P];
@@ -1196,6 +1199,7 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
         return row_sw ^ ((r & 1) ? S[0] : 0) ^ ((r & 2) ? S[1] : 0) ^ ((r & 4) ? S[2] : 0) ^ ((r & 8) ? S[3] : 0);
     };
     auto split = [&](int g0, int ab) {
+        if (!worker) return;
         unsigned h[2][P / 2], mm[2][P / 2], l[2][P / 2];
         if (g0 + row < ng) {
             const int bg = base_of(g0);
@@ -1232,6 +1236,7 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
     };
     auto reassemble = [&](int r0) {
         fence_after();
+        if (!worker) return;
         const uint32_t t0 = cx.tmem + lane_bits + 2 * P * cg;
         uint32_t z0[2 * P], z1[2 * P], z2[2 * P];
         ldN<2 * P>(t0, z0);
@@ -1248,7 +1253,7 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
         }
     };
     auto issue = [&](int ab) {
-        if (tid != 0 || (op.flags & OPF_TEST_NO_MMA)) return;
+        if (tid != kIssuer || (op.flags & OPF_TEST_NO_MMA)) return;
         fence_after();
 #pragma unroll
         for (int i = 0; i < 3; i++)
@@ -1275,7 +1280,7 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
     for (;; g0 += 128, ab ^= 1) {
         const int gn = g0 + 128;
         if (gn < ng) split(gn, ab ^ 1);  // overlaps the MMAs of round g0
-        const bool ok = wait(cx.mbar, cx.phase);
+        const bool ok = worker ? wait(cx.mbar, cx.phase) : true;
         cx.phase ^= 1;
         if (ok) reassemble(g0);
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
@@ -1298,6 +1303,9 @@ __device__ __forceinline__ void op_dense(Cx<float>* sm, int m, const DevOp& op, 
 // ---------------------------------------------------------------------------
 enum TileMode { MODE_F32 = 0, MODE_F64 = 1, MODE_DF = 2, MODE_TC = 3, MODE_T05 = 4, MODE_T32 = 5 };
 __host__ __device__ constexpr bool uses_tmem(int mode) { return mode == MODE_T05 || mode == MODE_T32; }
+__host__ __device__ constexpr int tile_threads(int mode) {
+    return mode == MODE_T32 ? t05::kCtaThreads : (mode == MODE_T05 ? t05::kThreads : kTileThreads);
+}
 
 template <int MODE>
 struct TileTraits;
@@ -1392,8 +1400,7 @@ __device__ __forceinline__ void apply_op(typename TileTraits<MODE>::Smem* sm, in
 // apply the pass's ops in order, scatter the tile back.  Persistent: each CTA
 // strides over the flattened tile space of all entries.
 template <int MODE, int KMAX>
-__global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads,
-                                  MODE == MODE_TC ? 2 : 1)
+__global__ void __launch_bounds__(tile_threads(MODE), MODE == MODE_TC ? 2 : 1)
     k_tile_pass(const BatchEntry* __restrict__ E, int n_entries, uint64_t total_tiles, const DevOp* __restrict__ ops,
                 const typename TileTraits<MODE>::Coef* __restrict__ coef) {
     using Tr = TileTraits<MODE>;
@@ -1624,9 +1631,11 @@ __global__ void __launch_bounds__(uses_tmem(MODE) ? t05::kThreads : kTileThreads
                 }
                 if (cx.failed) break;  // uniform: decided by a block-wide vote
             } else if constexpr (MODE == MODE_T32) {
-                if (op.kind == OP_DIAG)
-                    op_diag<float, t05::kLogThreads>(sm, m, op, reinterpret_cast<const Cx<float>*>(coef + op.coeff),
-                                                     base);
+                if (op.kind == OP_DIAG) {
+                    if (threadIdx.x < t05::kThreads)  // the issuing warp sits out the 512-thread sweep
+                        op_diag<float, t05::kLogThreads>(sm, m, op,
+                                                         reinterpret_cast<const Cx<float>*>(coef + op.coeff), base);
+                }
                 else {
                     const int* tab = n_ops <= kOpCache ? s_tab + o * t05::kTabInts : nullptr;
                     if (op.k <= 3) t32::op_dense<3>(sm, m, op, coef + op.coeff, cx, tab);  // smaller blocks are padded
@@ -1923,7 +1932,7 @@ static cudaError_t tile_pass_impl(const BatchEntry* d_entries, int n_entries, ui
         configured_dev = di.device;
     }
     if (smem > dyn_max) return cudaErrorInvalidValue;
-    const int threads = uses_tmem(MODE) ? t05::kThreads : kTileThreads;
+    const int threads = tile_threads(MODE);
     int per_sm = 1;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<MODE, KMAX>, threads, smem);
     if (e != cudaSuccess) return e;
