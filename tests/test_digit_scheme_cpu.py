@@ -1,10 +1,13 @@
-"""CPU pins of the integer identities the complex128 tcgen05 kernel rests on
-(exact digit split of Q56 fixed point, level sums in float32, re-assembly):
-each formula is checked bit for bit against plain integer arithmetic on
-random and extreme inputs, with the kernel's constants written out.
+"""CPU pins of the arithmetic the tcgen05 kernels rest on.
 
-The kernel (paper_2502_11385_gb300/csrc/kernels.cu, namespace t05) is not
-imported: these tests fix what its arithmetic must equal."""
+complex128 (exact digit split of Q56 fixed point, level sums in float32,
+re-assembly): each formula is checked bit for bit against plain integer
+arithmetic on random and extreme inputs, with the kernel's constants written
+out.  complex64 (bfloat16 triple split): the residuals are exact and the
+three parts, and the six part products kept, carry float32 accuracy.
+
+The kernels (paper_2502_11385_gb300/csrc/kernels.cu, namespaces t05 and t32)
+are not imported: these tests fix what their arithmetic must equal."""
 import math
 
 import numpy as np
@@ -128,3 +131,56 @@ def test_level_sums_exact_in_float32_with_preload():
         for k in rng.permutation(n):
             acc = np.float32(acc + np.float32(prods[k]))
         assert f32_bits(acc) - MAGIC_BITS == sum(prods)
+
+
+# ---------------------------------------------------------------------------
+# complex64: the bfloat16 triple split of float32 components
+# ---------------------------------------------------------------------------
+def bf16_rn(x):
+    """float32 -> bfloat16 (round to nearest, ties to even), returned as float32."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return r.astype(np.uint32).view(np.float32)
+
+
+def triple_split(x):
+    x = np.asarray(x, dtype=np.float32)
+    h = bf16_rn(x)
+    r1 = (x - h).astype(np.float32)
+    m = bf16_rn(r1)
+    r2 = (r1 - m).astype(np.float32)
+    return h, m, bf16_rn(r2), r1, r2
+
+
+def test_triple_split_residuals_exact_and_bounded():
+    rng = np.random.default_rng(21)
+    x = np.concatenate([rng.standard_normal(200000).astype(np.float32),
+                        (rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000)).astype(np.float32),
+                        np.float32([1.0, -1.0, 0.5, 3.0, 1.0 / 3.0, 2.0 ** -100])])
+    h, m, l, r1, r2 = triple_split(x)
+    x64, h64, m64, l64 = (v.astype(np.float64) for v in (x, h, m, l))
+    # both residuals are exact in float32
+    assert np.array_equal(r1.astype(np.float64), x64 - h64)
+    assert np.array_equal(r2.astype(np.float64), x64 - h64 - m64)
+    # the three parts carry float32 accuracy
+    err = np.abs(x64 - h64 - m64 - l64)
+    assert np.all(err <= 2.0 ** -24 * np.abs(x64))
+
+
+def test_triple_split_products_keep_float32_accuracy():
+    """Dot products from the six part products with i + j <= 2 (levels 0..2,
+    the dropped ones below 2^-24 relative), summed in float32, stay within a
+    few float32 ulps of the exact result."""
+    rng = np.random.default_rng(22)
+    for _ in range(200):
+        n = int(rng.integers(8, 65))
+        a = rng.standard_normal(n).astype(np.float32)
+        b = rng.standard_normal(n).astype(np.float32)
+        pa, pb = triple_split(a)[:3], triple_split(b)[:3]
+        acc = np.float32(0)
+        for i in range(3):
+            for j in range(3 - i):
+                acc = np.float32(acc + np.float32(np.dot(pa[i].astype(np.float64), pb[j].astype(np.float64))))
+        exact = float(np.dot(a.astype(np.float64), b.astype(np.float64)))
+        scale = float(np.dot(np.abs(a.astype(np.float64)), np.abs(b.astype(np.float64))))
+        assert abs(float(acc) - exact) <= 8 * 2.0 ** -24 * scale
