@@ -106,6 +106,7 @@ int default_tile(int dt, int arith = SV_ARITH_NATIVE) {
     if (dt == SV_C64) return arith == SV_ARITH_TC ? 14 : 13;
     return arith == SV_ARITH_TC ? 13 : 12;
 }
+constexpr int kGateDown = 36;   // pre-scale of the norm that gates caller-supplied states
 int coalesce_of(int dt) { return dt == SV_C64 ? 5 : 4; }
 int max_tile(int dt, const svk::DevInfo& di) {
     int m = dt == SV_C64 ? 14 : 13;
@@ -725,15 +726,33 @@ int sv_apply_circuit(sv_state* s, const sv_gate* g, size_t ng, const sv_run_opts
     const double t1 = now_ms();
     int arith = resolve_arith(s->dt, o, s->n);
     if (s->dt == SV_C128 && is_tc(arith) && s->foreign) {
-        // caller-supplied amplitudes: the fixed-point tile needs |re|, |im| <= 1
-        SV_TRY(ensure(&s->d_red, &s->d_red_cap, 256, false));
+        // caller-supplied amplitudes: the fixed-point tile needs every component
+        // of every state the circuit passes through to stay within [-1, 1].  A
+        // norm of at most 1 guarantees it (the blocks are unitary, so the norm
+        // is kept and bounds every component); a bound on the components alone
+        // does not (one Hadamard takes (1, 1) to (sqrt 2, 0)).  The max-abs pass
+        // comes first so that the exact fixed-point norm, pre-scaled by 2^-36,
+        // cannot overflow (at most 2^34 terms of at most 2 each).
+        SV_TRY(ensure(&s->d_red, &s->d_red_cap, svk::norm_scratch_bytes(s->di) + 256, false));
         SV_TRY(svk::launch_max_abs_c128(s->amp, s->n, (unsigned long long*)s->d_red, s->stream, s->di));
         unsigned long long bits = 0;
         SV_TRY(cudaMemcpyAsync(&bits, s->d_red, 8, cudaMemcpyDeviceToHost, s->stream));
         SV_TRY(cudaStreamSynchronize(s->stream));
         double mx;
         std::memcpy(&mx, &bits, 8);
-        if (mx <= 1.0) s->foreign = false;  // evolution by unitaries keeps it so
+        bool ok = mx <= 1.0;
+        if (ok) {
+            const size_t scratch = svk::norm_scratch_bytes(s->di);
+            double* d_out = (double*)((unsigned char*)s->d_red + scratch);
+            double nrm = 0;
+            SV_TRY(svk::launch_norm(s->dt, s->amp, s->n, s->d_red, d_out, s->stream, s->di, kGateDown));
+            SV_TRY(cudaMemcpyAsync(&nrm, d_out, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+            SV_TRY(cudaStreamSynchronize(s->stream));
+            // a float64-normalised state may exceed 1 by rounding; 2^-40 of slack
+            // keeps components below 1 + 2^-41, far inside the digits' range
+            ok = std::ldexp(nrm, kGateDown) <= 1.0 + std::ldexp(1.0, -40);
+        }
+        if (ok) s->foreign = false;  // evolution by unitaries keeps the norm
         else arith = SV_ARITH_DF64;
     }
     if (arith != resolve_arith(s->dt, o, s->n)) {  // re-plan for double-float arithmetic

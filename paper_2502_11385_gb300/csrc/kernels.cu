@@ -715,6 +715,7 @@ constexpr unsigned kHalf3072 = 0x6A00u, kHalf4096 = 0x6C00u;
 constexpr int kBiasRows = 7 * 32;  // N of the widest accumulator (7 R, R = 32)
 constexpr unsigned long long kWaitNs = 1000000000ull;  // a bounded wait gives up after one second
 constexpr unsigned kWaitPolls = 1u << 26;                 // and after this many polls in any case
+constexpr unsigned kSuspendNs = 20000;                    // longest sleep of one poll
 
 __device__ int g_fault;  // set when a bounded wait ran out (read and cleared by the host)
 
@@ -759,14 +760,15 @@ __device__ __forceinline__ bool wait(uint32_t mbar, uint32_t parity) {
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < kWaitPolls; it++) {
         uint32_t done;
+        // the thread sleeps until the phase completes or kSuspendNs pass
         asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done)
-            : "r"(mbar), "r"(parity)
+            : "r"(mbar), "r"(parity), "n"(kSuspendNs)
             : "memory");
         if (done) return true;
-        if ((it & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
+        if ((it & 15) == 15 && global_ns() - t0 > kWaitNs) return false;
     }
     return false;
 }
@@ -993,28 +995,27 @@ __device__ __forceinline__ void op_dense(Q2* sm, int m, const DevOp& op, const u
         const uint32_t t0 = cx.tmem + lane_bits + mt_t * 128 + 8 * cg;
         // out = P0 2^32 + P1 2^16 + P2 + level 6 (mod 2^64), the offsets removed by one constant
         unsigned long long y[8];
-        uint32_t a[8], b[8];
-        ld8(t0, a);
-        ld8(t0 + R, b);
+        uint32_t z[4][8];
+        ld8(t0, z[0]);
+        ld8(t0 + R, z[1]);
+        ld8(t0 + 2 * R, z[2]);
+        ld8(t0 + 3 * R, z[3]);
         ld_wait();
 #pragma unroll
-        for (int e = 0; e < 8; e++)
-            y[e] = ((unsigned long long)(level_pair(a[e], b[e]) + (unsigned)(kLevelBias >> 32)) << 32) |
+        for (int e = 0; e < 8; e++) {
+            y[e] = ((unsigned long long)(level_pair(z[0][e], z[1][e]) + (unsigned)(kLevelBias >> 32)) << 32) |
                    (unsigned)kLevelBias;
-        ld8(t0 + 2 * R, a);
-        ld8(t0 + 3 * R, b);
+            y[e] = mad_wide(level_pair(z[2][e], z[3][e]), 65536u, y[e]);
+        }
+        ld8(t0 + 4 * R, z[0]);
+        ld8(t0 + 5 * R, z[1]);
+        ld8(t0 + 6 * R, z[2]);
         ld_wait();
 #pragma unroll
-        for (int e = 0; e < 8; e++) y[e] = mad_wide(level_pair(a[e], b[e]), 65536u, y[e]);
-        ld8(t0 + 4 * R, a);
-        ld8(t0 + 5 * R, b);
-        ld_wait();
-#pragma unroll
-        for (int e = 0; e < 8; e++) y[e] = mad_wide(level_pair(a[e], b[e]), 1u, y[e]);
-        ld8(t0 + 6 * R, a);
-        ld_wait();
-#pragma unroll
-        for (int e = 0; e < 8; e++) y[e] = mad_wide(level6(a[e]), 1u, y[e]);
+        for (int e = 0; e < 8; e++) {
+            y[e] = mad_wide(level_pair(z[0][e], z[1][e]), 1u, y[e]);
+            y[e] = mad_wide(level6(z[2][e]), 1u, y[e]);
+        }
         if (r0 + loc < ng) {
             const int bg = base_of(r0);
 #pragma unroll
@@ -1720,13 +1721,14 @@ __device__ __forceinline__ double prob_of(Cx<R> v) {
     return fma(re, re, im * im);  // exact products for float inputs, one rounding
 }
 
-// x >= 0 (x < 16) as an unsigned 128-bit fixed-point number in units of 2^-124.
-__device__ __forceinline__ unsigned __int128 to_fixed(double x) {
+// x 2^-down (x >= 0, x 2^-down < 16) as an unsigned 128-bit fixed-point
+// number in units of 2^-124.
+__device__ __forceinline__ unsigned __int128 to_fixed(double x, int down = 0) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const int e = (int)((b >> 52) & 0x7ff);
     if (e == 0) return 0;  // zero or subnormal (below 2^-1022): below the grid
     const unsigned long long mant = (b & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = e - 1075 + 124;
+    const int sh = e - 1075 + 124 - down;
     if (sh >= 0) return (unsigned __int128)mant << sh;
     if (sh <= -53) return 0;
     return (unsigned __int128)(mant >> (-sh));
@@ -1779,11 +1781,12 @@ __global__ void k_probs(const Cx<R>* __restrict__ a, uint64_t i0, uint64_t len, 
 }
 
 template <typename R>
-__global__ void k_norm_partial(const Cx<R>* __restrict__ a, uint64_t dim, unsigned long long* __restrict__ part) {
+__global__ void k_norm_partial(const Cx<R>* __restrict__ a, uint64_t dim, unsigned long long* __restrict__ part,
+                               int down) {
     unsigned __int128 acc = 0;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride)
-        acc += to_fixed(prob_of<R>(a[i]));
+        acc += to_fixed(prob_of<R>(a[i]), down);
     acc = block_sum128(acc);
     if (threadIdx.x == 0) {
         part[2 * blockIdx.x] = (unsigned long long)acc;
@@ -2020,14 +2023,14 @@ static constexpr int kNormThreads = 256;
 size_t norm_scratch_bytes(const DevInfo& di) { return (size_t)di.sms * 8 * 2 * sizeof(unsigned long long); }
 
 cudaError_t launch_norm(int dt, const void* amp, int n, void* d_scratch, double* d_out, cudaStream_t s,
-                        const DevInfo& di) {
+                        const DevInfo& di, int down) {
     const uint64_t dim = 1ull << n;
     const unsigned grid = grid_for(dim, kNormThreads, di, 8);
     auto* part = (unsigned long long*)d_scratch;
     if (dt == SV_C64)
-        k_norm_partial<float><<<grid, kNormThreads, 0, s>>>((const Cx<float>*)amp, dim, part);
+        k_norm_partial<float><<<grid, kNormThreads, 0, s>>>((const Cx<float>*)amp, dim, part, down);
     else
-        k_norm_partial<double><<<grid, kNormThreads, 0, s>>>((const Cx<double>*)amp, dim, part);
+        k_norm_partial<double><<<grid, kNormThreads, 0, s>>>((const Cx<double>*)amp, dim, part, down);
     k_norm_final<<<1, 1024, 0, s>>>(part, (int)grid, d_out);
     return cudaGetLastError();
 }

@@ -49,11 +49,13 @@ cudaError_t launch_max_abs_c128(const void* amp, int n, unsigned long long* d_ou
 cudaError_t launch_probs(int dt, const void* amp, uint64_t i0, uint64_t len, double* p,
                          cudaStream_t s, const DevInfo& di);
 
-// *d_out = sum_i |amp_i|^2 via exact 128-bit fixed-point accumulation (K7, norm part).
-// d_scratch needs norm_scratch_bytes(di) bytes.
+// *d_out = 2^-down sum_i |amp_i|^2 via exact 128-bit fixed-point
+// accumulation (K7, norm part); the scaled sum must stay below 16 (down = 0
+// for normalised states; down = 36 bounds any state whose components are at
+// most 1 in magnitude).  d_scratch needs norm_scratch_bytes(di) bytes.
 size_t norm_scratch_bytes(const DevInfo& di);
 cudaError_t launch_norm(int dt, const void* amp, int n, void* d_scratch, double* d_out,
-                        cudaStream_t s, const DevInfo& di);
+                        cudaStream_t s, const DevInfo& di, int down = 0);
 
 // Marginal over the qubits of qubit_mask into d_out (2^popcount doubles);
 // d_bins needs 2 * 8 * 2^popcount bytes.
