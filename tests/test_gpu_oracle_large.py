@@ -1,0 +1,136 @@
+"""GPU parity at large widths, element by element against the CPU oracle.
+
+- Random circuits over the whole gate set on 22, 24, 26 and 28 qubits with the
+  automatic options: the tensor-core modes (complex128 digits, 13-qubit tiles;
+  complex64 triple split from 23 qubits), several passes whose tiles hold high
+  qubits, and byte offsets beyond 2^32 (n >= 28 for complex128).
+- The benchmark circuit itself (30 qubits, complex128, GHZ prefix + brickwork
+  depth 20, seed 2), all 2^30 amplitudes against the oracle (marked slow: the
+  oracle applies its 920 gates one by one to a 16 GiB state on the host cores,
+  several minutes).
+
+Tolerances as in the rest of the suite: max |delta a| <= 1e-12 (complex128),
+<= 1e-5 (complex64).  The relative L2 error |delta a| / |a| is printed."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2502_11385_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = {"c128": 1e-12, "c64": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def sv():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_2502_11385_gb300 import sv as _sv
+    return _sv
+
+
+def _host_bytes_free():
+    return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+
+
+def _random_circuit(n, count, seed):
+    """Gates of every kind on qubits drawn over the whole register, angles in
+    [-7, 7): every tile pass sees high qubits."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for _ in range(count):
+        op = int(rng.integers(0, 14))
+        q0 = int(rng.integers(0, n))
+        q1 = -1
+        if op >= W.CX:
+            q1 = int(rng.choice([q for q in range(n) if q != q0]))
+        rows.append((op, q0, q1, *rng.uniform(-7, 7, 3)))
+    return W.gates(rows)
+
+
+def _compare(got, ref, chunk=1 << 24):
+    """max |got - ref| and the relative L2 error, chunk by chunk (no full-size
+    temporaries)."""
+    mx, num, den = 0.0, 0.0, 0.0
+    for i in range(0, ref.size, chunk):
+        d = got[i:i + chunk].astype(np.complex128) - ref[i:i + chunk]
+        a = np.abs(d)
+        mx = max(mx, float(a.max()))
+        num += float(np.dot(a, a))
+        r = np.abs(ref[i:i + chunk])
+        den += float(np.dot(r, r))
+    return mx, (num / den) ** 0.5
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("n", [22, 24, 26, 28])
+def test_random_circuit_against_oracle_large(sv, n, dtype):
+    g = _random_circuit(n, 60, 5000 + n)
+    with sv.State(n, dtype) as s:
+        s.apply_circuit(g)
+        st = s.stats()
+        got = s.amplitudes()
+    if dtype == "c128":
+        assert st["arith"] == sv.ARITH_TC and st["tile_qubits"] == 13
+    elif n >= 23:
+        assert st["arith"] == sv.ARITH_TC
+    assert st["n_passes"] > 1
+    ref = oracle.run(n, g)
+    mx, rel = _compare(got, ref)
+    print(f"n={n} {dtype}: passes={st['n_passes']} max|da|={mx:.3e} rel L2={rel:.3e}")
+    assert mx <= TOL[dtype], (n, dtype, mx)
+
+
+@pytest.mark.slow
+def test_bench_circuit_30q_c128_every_amplitude(sv):
+    """The benchmark's own circuit and options (GHZ + brickwork depth 20, seed
+    2, 920 gates, complex128, automatic arithmetic: tcgen05 digits), compared
+    with the oracle amplitude by amplitude."""
+    n = 30
+    if _host_bytes_free() < 48 * 2**30:
+        pytest.skip("the oracle needs about 48 GiB of free host memory at 30 qubits")
+    g = W.workload_ghz_brickwork(n, 20, 2)
+    with sv.State(n, "c128") as s:
+        s.apply_circuit(g)
+        st = s.stats()
+        got = s.amplitudes()
+    assert st["arith"] == sv.ARITH_TC
+    ref = oracle.run(n, g)
+    mx, rel = _compare(got, ref)
+    print(f"30q bench circuit: passes={st['n_passes']} blocks={st['n_blocks']} "
+          f"max|da|={mx:.3e} rel L2={rel:.3e}")
+    assert mx <= TOL["c128"], mx
+
+
+FAMILY_CASES = {
+    # the paper's benchmark families (Sec. V-B), 20-22 qubits
+    "adder": lambda: W.cuccaro_adder(10, 0x2A5, 0x1C7),           # 22 qubits
+    "aqft": lambda: W.aqft(22, 5, 0x2345677 & ((1 << 22) - 1)),   # partial degree
+    "bv": lambda: W.bernstein_vazirani(22, 0x2CB8F0 & ((1 << 21) - 1)),
+    "hwea": lambda: W.hwea(22, 4, 6),
+    "supremacy": lambda: W.supremacy(4, 5, 16, 7),                # 20 qubits, 4 x 5 grid
+}
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
+@pytest.mark.parametrize("family", sorted(FAMILY_CASES))
+def test_family_against_oracle(sv, family, dtype):
+    """Each family through the default options (tensor-core arithmetic at
+    these widths for complex128; float32 FMAs for complex64 below 23 qubits,
+    so the complex64 triple split is run explicitly too)."""
+    g = FAMILY_CASES[family]()
+    n = max(int(g["q0"].max()), int(g["q1"].max())) + 1
+    ref = oracle.run(n, g)
+    modes = [0] if dtype == "c128" else [0, sv.ARITH_TC]
+    for arith in modes:
+        with sv.State(n, dtype) as s:
+            s.apply_circuit(g, sv.run_opts(arith=arith))
+            got = s.amplitudes()
+        mx, rel = _compare(got, ref)
+        print(f"{family} {n}q {dtype} arith={arith}: max|da|={mx:.3e} rel L2={rel:.3e}")
+        assert mx <= TOL[dtype], (family, dtype, arith, mx)

@@ -55,3 +55,26 @@ def test_noalloc_marginal_rejects_masks_beyond_static_scratch(sv):
         assert e.value.code == sv.SV_ERR_QUBIT
         out = sv.marginal_probabilities_noalloc(s.device_ptr, n, "c64", (1 << 16) - 1)  # the maximum
         assert abs(out[0] - 0.5) < 1e-6 and abs(out[-1] - 0.5) < 1e-6
+
+
+def test_noalloc_marginal_leaves_free_device_memory_unchanged(sv):
+    """The entry point's defining property: after the first calls (which look
+    the static scratch up and load the kernels), repeated calls change the
+    device's free memory by nothing, for host and device outputs alike."""
+    import torch
+    n = 16
+    with sv.State(n, "c128") as s:
+        s.apply_circuit(W.concat(W.ghz_prefix(n), W.brickwork(n, 4, 9)))
+        ptr = s.device_ptr
+        mask = 0b1011000000110111
+        dev = torch.empty(1 << bin(mask).count("1"), dtype=torch.float64, device="cuda")
+        first = sv.marginal_probabilities_noalloc(ptr, n, "c128", mask)
+        sv.marginal_probabilities_noalloc(ptr, n, "c128", mask, out=dev)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(5):
+            host = sv.marginal_probabilities_noalloc(ptr, n, "c128", mask)
+            sv.marginal_probabilities_noalloc(ptr, n, "c128", mask, out=dev)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert np.array_equal(host, first)
