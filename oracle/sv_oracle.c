@@ -178,10 +178,6 @@ long oracle_run(int n, double* psi_ri, const or_gate* g, size_t ng)
     return oracle_apply(n, psi_ri, g, ng);
 }
 
-/* Same for a complex64 state: the amplitudes are widened to complex128,
- * simulated, and the result is returned in complex128 (the reference every
- * complex64 result is compared with). */
-
 /* p_i = re^2 + im^2. */
 void oracle_probabilities(int n, const double* psi_ri, double* p)
 {
