@@ -72,15 +72,25 @@ typedef struct {
  *                    the FP32 units (error-free TwoProd / TwoSum transforms,
  *                    Dekker 1971; Joldes, Muller, Popescu 2017), about 47
  *                    significant bits per operation.
- *   SV_ARITH_TC:     float64 storage, the state held in Q62 fixed point in
- *                    shared memory, fused-block products on the tensor cores
- *                    (tcgen05.mma, accumulators in tensor memory) with an
- *                    exact split of both operands into seven balanced 8-bit
- *                    digits: bfloat16 digit products, exact float32 sums per
- *                    digit level, levels 0..6 re-assembled in int64 (error
- *                    about 1e-16 per block product, see the tile-pass notes
- *                    in the kernels); requires amplitude components of
- *                    magnitude at most 1 (any normalised state).
+ *   SV_ARITH_TC:     float64 storage; inside a call the state is held in Q56
+ *                    fixed point (x * 2^56 in an int64 per component, also in
+ *                    HBM between the call's passes) and fused-block products
+ *                    run on the tensor cores (tcgen05.mma, accumulators in
+ *                    tensor memory) with an exact split of both operands into
+ *                    seven balanced 8-bit digits held as float16: exact digit
+ *                    products, exact float32 sums per digit level, levels 0..6
+ *                    re-assembled in 64-bit integers (error below 2^-50 per
+ *                    component and block product, an absolute bound: about
+ *                    2^-35 relative to a 30-qubit amplitude of typical size
+ *                    2^-15).  Precondition: every component of every state the
+ *                    call passes through lies in [-1, 1], which a state of norm
+ *                    at most 1 guarantees (the blocks are unitary).  States
+ *                    evolved from a basis state satisfy it; for caller-supplied
+ *                    amplitudes (sv_set_amplitudes, sv_create_on) the first
+ *                    call measures the norm exactly and uses SV_ARITH_DF64 if it
+ *                    exceeds 1 + 2^-40.  A block whose digit sums could leave
+ *                    the exact float32 range (none of the unitary blocks seen)
+ *                    also falls back to SV_ARITH_DF64.
  *   SV_ARITH_TC_SYNC: the same digit products on the warp-level mma.sync
  *                    path (unsigned lower digits), kept as the measured
  *                    baseline of the tensor-memory kernel.
@@ -89,12 +99,7 @@ typedef struct {
  *                    pipe runs at about 1/70 of the FP32 pipe, so native
  *                    FP64 is never the automatic choice).  SV_ARITH_TC and
  *                    SV_ARITH_TC_SYNC fall back to SV_ARITH_DF64 below 8
- *                    qubits.  Amplitudes supplied by the caller
- *                    (sv_set_amplitudes, sv_create_on) are checked once:
- *                    if a component exceeds 1 in magnitude the call uses
- *                    SV_ARITH_DF64 instead; so does a block whose digit sums
- *                    could exceed the exact float32 range (none for unitary
- *                    blocks).
+ *                    qubits.
  * complex64 states: SV_ARITH_NATIVE (and SV_ARITH_DF64 / SV_ARITH_TC_SYNC)
  * compute in float32 FMAs; SV_ARITH_TC splits every float32 component into
  * three bfloat16 parts and forms the six part products of float32 accuracy
@@ -134,12 +139,17 @@ typedef struct {
 typedef struct sv_state sv_state;
 
 /* Bytes of a state: 2^n * 8 (SV_C64) or 2^n * 16 (SV_C128); 0 if n is not in
- * 1..34 or dt is not a sv_dtype.  Host-only; Table III's sizes. */
+ * 1..34 or dt is not a sv_dtype.  Host-only; the memory column of Table III
+ * (complex128: 2^n x 16 bytes, 30 qubits = 17.18 GB). */
 size_t sv_state_bytes(int n_qubits, int dt);
 
 /* Creates an n-qubit state (1 <= n <= 34) in a device buffer the library
  * allocates and owns, initialised to |0...0>, on the current CUDA device and
- * a stream the library creates.  SV_ERR_OOM if it does not fit. */
+ * a stream the library creates.  SV_ERR_OOM if it does not fit.  The
+ * statevector a simulation starts from (Sec. III-B: 2^n complex amplitudes,
+ * memory doubling per qubit; Listing 3 runs the circuit on one such state,
+ * the device chosen at run time); 34 qubits is the largest width the paper
+ * simulates (Sec. V-B, Table III). */
 int sv_create(int n_qubits, int dt, sv_state** out);
 
 /* Wraps a caller-owned device buffer (for example a torch tensor) of
@@ -150,7 +160,9 @@ int sv_create(int n_qubits, int dt, sv_state** out);
 int sv_create_on(void* dev_ptr, size_t bytes, int n_qubits, int dt,
                  void* cuda_stream, sv_state** out);
 
-/* Frees the handle and, unless created by sv_create_on, its buffer. */
+/* Frees the handle and, unless created by sv_create_on, its buffer.  The
+ * paper has no counterpart (Aer frees its state when the run ends,
+ * Listing 3); the caller decides here how long a state stays resident. */
 void sv_destroy(sv_state* s);
 
 /* Points a handle made by sv_create_on at another caller-owned buffer (same
@@ -162,7 +174,10 @@ int sv_dtype_of(const sv_state* s);
 /* Device pointer of the amplitudes (for zero-copy interop). */
 void* sv_device_ptr(const sv_state* s);
 
-/* Sets the state to the basis state |basis_index> (< 2^n). */
+/* Sets the state to the basis state |basis_index> (< 2^n): the initial
+ * state of a run (|0...0>, Listing 3) or a cut-subcircuit variant's
+ * computational-basis input (the Evaluator's initialisations, Sec. III-A,
+ * Eqs. 3.5-3.6).  SV_ERR_ARG if basis_index >= 2^n. */
 int sv_reset(sv_state* s, uint64_t basis_index);
 
 /* Applies gates[0..n_gates) in list order (validated first: SV_ERR_ARG for an
@@ -199,7 +214,8 @@ int sv_marginal_probabilities(sv_state* s, uint64_t qubit_mask, double* out,
  *               of dtype dt), read only; no handle is needed.
  *   out:        2^popcount(mask) float64, host memory unless out_is_device.
  *   cuda_stream: the cudaStream_t to run on (NULL = legacy default stream);
- *               the call returns after the result is in out.
+ *               the call synchronises that stream and returns after the
+ *               result is in out, so it cannot be recorded into a CUDA graph.
  * It allocates nothing: its scratch is a static 1.5 MiB device array inside
  * the library (held on every GPU that loads the library until exit), so the
  * mask may select at most 16 qubits (SV_ERR_SIZE beyond).  The first call on
@@ -211,12 +227,20 @@ int sv_marginal_probabilities_noalloc(const void* amplitudes, int n_qubits, int 
                                       int out_is_device, void* cuda_stream);
 
 /* Copies the amplitudes (sv_state_bytes bytes, in the state's dtype) out, or
- * in (sv_set_amplitudes: checkpoint restore). */
+ * in (sv_set_amplitudes: checkpoint restore).  The full statevector output a
+ * simulation can return beside the probabilities (Sec. III-B; the paper's
+ * per-circuit results are written to disk for later steps, Sec. IV-A).
+ * bytes must equal sv_state_bytes (else SV_ERR_SIZE); the buffer is host
+ * memory unless *_is_device.  Amplitudes set from outside are checked as
+ * SV_ARITH_TC describes before the next tensor-core call. */
 int sv_amplitudes(sv_state* s, void* out, size_t bytes, int out_is_device);
 int sv_set_amplitudes(sv_state* s, const void* in, size_t bytes, int in_is_device);
 
 /* sum_i |a_i|^2, accumulated exactly in 128-bit fixed point on the device
- * (order-independent, so bitwise reproducible) and rounded once to float64. */
+ * (order-independent, so bitwise reproducible) and rounded once to float64.
+ * The sum of the probability vector Listing 3 returns (1 for a normalised
+ * state; Sec. III-A's reconstruction assumes normalised subcircuit
+ * distributions).  Valid for sums below 16 (SV_ARITH_TC states have norm 1). */
 int sv_norm(sv_state* s, double* out);
 
 /* Statistics of the last sv_apply_circuit on this handle. */
