@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--serve-wmax", type=int, default=30)
     ap.add_argument("--serve-sample", type=int, default=300,
                     help="requests of the serving sample added to the default line")
+    ap.add_argument("--analytic-model", action="store_true",
+                    help="plan with the analytic cost model instead of the tables measured on this GPU")
     ap.add_argument("--no-forms", action="store_true",
                     help="leave the batching and serving measurements out of the default line")
     return ap.parse_args()
@@ -540,6 +542,12 @@ def main():
 
     n, dt = args.n, args.dtype
     gates, wl_name = workload_gates(args, W)
+    # the measured autotuner: this GPU's cost tables (cached JSON, measured on
+    # first use) steer the planner's choice of fusion width and variant
+    tuned = {}
+    if not args.analytic_model:
+        from paper_2502_11385_gb300 import tune
+        tuned = tune.ensure()
     ctype = torch.complex128 if dt == "c128" else torch.complex64
     amp_bytes = 16 if dt == "c128" else 8
     state_bytes = (1 << n) * amp_bytes
@@ -679,6 +687,8 @@ def main():
                       "arith": arith_name,
                       "fuse_k": s0["fuse_k"], "tile_qubits": s0["tile_qubits"], "passes": passes,
                       "blocks": s0["n_blocks"], "l2": f"state {state_bytes >> 30} GiB > L2, no flush needed",
+                      "planner": ("cost tables measured on this GPU (sv_calibrate, cached)" if tuned
+                                  else "analytic cost model"),
                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
            "frac_of_measured_hbm": round(value / peaks["hbm_gbs"], 4),
            "frac_of_8tbs": round(value / 8000.0, 4),

@@ -360,6 +360,45 @@ int sv_cut_variants(int dt, const sv_gate* body_a, size_t n_a, int width_a,
                     double* const* up_out, double* const* down_out,
                     int outs_on_device, const sv_run_opts* opts);
 
+/* Measured autotuner (the paper's analogue: Aer's blocking_qubits and the
+ * Evaluator's worker count, both set by trial, Sec. IV-A, Listing 4).  The
+ * planner picks the fusion width and the fusion variant for each circuit by
+ * a cost model; by default an analytic one, or, once sv_set_costs installed
+ * a table for the (dtype, arithmetic) pair, these costs measured on the
+ * device.  All figures are picoseconds per amplitude of the state (so a 2^n
+ * state pays 2^n times each):
+ *   pass_ps       one tile pass that applies nothing (the tile's HBM read
+ *                 and write and its conversions);
+ *   dense_ps[k]   one dense block of k qubits (k = 1..5; 0 unused); the
+ *                 tensor-core modes pad blocks below 3 qubits to 3, and the
+ *                 complex128 digit mode has no 5-qubit blocks (0 there);
+ *   diag_ps       one diagonal block with general phases;
+ *   sign_ps       one diagonal block of signs only (CZ / Z);
+ *   perm_ps[k]    one permutation block of k qubits with quarter phases.
+ * A Kronecker block costs k dense_ps[1] outside the tensor-core modes and
+ * dense_ps[k] in them; a permutation block with other phases adds diag_ps. */
+typedef struct {
+    int32_t dt, arith;           /* the pair measured (arith resolved, not AUTO) */
+    int32_t n_qubits, tile_qubits;  /* the calibration state and its tiles     */
+    double pass_ps;
+    double dense_ps[6];
+    double diag_ps, sign_ps;
+    double perm_ps[6];
+} sv_costs;
+
+/* Measures the table on the current device: single-pass synthetic plans on
+ * a 24-qubit (complex128) or 25-qubit (complex64) state, timed with CUDA
+ * events, each the fastest of three runs.  arith is resolved as for a
+ * 24-qubit state (SV_ARITH_AUTO gives the tensor-core modes).  Allocates the
+ * state and frees it before returning; SV_ERR_OOM if it does not fit. */
+int sv_calibrate(int dt, int arith, sv_costs* out);
+
+/* Installs (or, with costs = NULL, removes) the measured table for the pair
+ * (dt, arith), where arith is the resolved mode the table was measured for
+ * (SV_ARITH_NATIVE, SV_ARITH_DF64 or SV_ARITH_TC).  Process-wide; host only
+ * (no device call).  Plans made afterwards for that pair use it. */
+int sv_set_costs(int dt, int arith, const sv_costs* costs);
+
 /* Static description of a status code. */
 const char* sv_status_str(int status);
 

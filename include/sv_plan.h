@@ -35,11 +35,15 @@ typedef struct {
 } sv_plan_summary;
 int sv_plan_summary_get(const sv_plan* p, sv_plan_summary* out);
 
-/* Block b: kind (0 dense, 1 diagonal), k, its qubits (ascending; matrix bit j
- * is qubits[j]), the input-gate indices it holds (up to cap_gates written,
- * *n_gates = total), and its matrix as interleaved (re, im) float64 --
- * (2^k)^2 row-major entries for dense, 2^k for diagonal (up to cap_mat
- * doubles written). */
+/* Block b: kind (0 dense, 1 diagonal, 2 permutation -- one nonzero per row,
+ * applied by moving amplitudes -- or 3 Kronecker -- a tensor product of
+ * one-qubit matrices, applied as one butterfly per qubit outside the
+ * tensor-core modes), k, its qubits (ascending; matrix bit j is qubits[j]),
+ * the input-gate indices it holds (up to cap_gates written, *n_gates =
+ * total), and its matrix as interleaved (re, im) float64 -- 2^k entries for
+ * diagonal, (2^k)^2 row-major for the other kinds (up to cap_mat doubles
+ * written).  The classes are those of the fusion step's block analysis (the
+ * transpile phase Aer runs before simulating, Sec. III-B). */
 int sv_plan_block(const sv_plan* p, int b, int* kind, int* k, int* qubits,
                   int* n_gates, int* gate_ids, size_t cap_gates,
                   double* mat, size_t cap_mat);

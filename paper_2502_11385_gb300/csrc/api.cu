@@ -12,8 +12,10 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "device_types.hpp"
@@ -141,6 +143,19 @@ int resolve_arith(int dt, const sv_run_opts* o, int n = 34) {
 
 bool is_tc(int arith) { return arith == SV_ARITH_TC || arith == SV_ARITH_TC_SYNC; }
 
+// Device-measured cost tables (sv_calibrate / sv_set_costs), per (dtype,
+// resolved arithmetic); the planner's cost model when one is installed.
+std::mutex g_costs_mu;
+std::map<std::pair<int, int>, sv_costs> g_costs;
+
+bool measured_costs(int dt, int arith, sv_costs* out) {
+    std::lock_guard<std::mutex> lk(g_costs_mu);
+    auto it = g_costs.find({dt, arith});
+    if (it == g_costs.end()) return false;
+    *out = it->second;
+    return true;
+}
+
 svp::Plan plan_for(int n, int dt, const sv_gate* g, size_t ng, const sv_run_opts* o, int smem_max_m) {
     int k = o ? o->max_fuse_k : 0;
     if (k < 0) k = 0;
@@ -152,6 +167,8 @@ svp::Plan plan_for(int n, int dt, const sv_gate* g, size_t ng, const sv_run_opts
     m = std::min(m, c + 10);
     m = std::max(m, c + svp::kMaxFuse);
     svp::Machine mc;
+    sv_costs measured;
+    if (measured_costs(dt, arith, &measured)) mc.measured = &measured;
     int ak = arith == SV_ARITH_TC ? svp::AK_TC32 : svp::AK_FP32;
     if (dt == SV_C128) ak = arith == SV_ARITH_DF64 ? svp::AK_DF64 : (is_tc(arith) ? svp::AK_TC : svp::AK_FP64);
     return svp::make_plan(n, g, ng, k, m, c, amp_bytes(dt), ak, mc);
@@ -412,59 +429,127 @@ void lower(const svp::Plan& P, Lowered& L, int arith = SV_ARITH_NATIVE, bool inj
             }
         }
         dp.op0 = (int32_t)L.ops.size();
-        for (int bi : ps.blocks) {
-            const svp::Block& b = P.blocks[bi];
-            DevOp op;
-            std::memset(&op, 0, sizeof(op));
-            op.kind = b.kind == svp::BK_DIAG ? svk::OP_DIAG : svk::OP_DENSE;
-            op.k = b.k;
-            op.coeff = (int32_t)L.coef.size();
-            op.flags = (b.kind == svp::BK_DIAG && b.sign_only) ? svk::OPF_SIGN_ONLY : 0;
-            for (int j = 0; j < b.k; j++) {
-                op.pos[j] = pos_of[b.qubits[j]];
-                op.qbit[j] = b.qubits[j];
-            }
+        // one op per block; a permutation block with other than quarter phases
+        // adds a diagonal op after it, and a Kronecker block outside the
+        // tensor-core modes becomes one butterfly per qubit
+        auto emit_diag = [&](DevOp op, const std::vector<svp::cd>& d, bool sign_only) {
+            op.kind = svk::OP_DIAG;
+            op.flags = sign_only ? svk::OPF_SIGN_ONLY : 0;
             if (L.is_tc) {
                 op.coeff = (int32_t)L.tc.size();
-                if (op.kind == svk::OP_DIAG && c64) {  // float pairs, two entries per 16 bytes
-                    for (size_t e = 0; e < b.mat.size(); e += 2) {
-                        float f[4] = {(float)b.mat[e].real(), (float)b.mat[e].imag(), 0.f, 0.f};
-                        if (e + 1 < b.mat.size()) {
-                            f[2] = (float)b.mat[e + 1].real();
-                            f[3] = (float)b.mat[e + 1].imag();
+                if (c64) {  // float pairs, two entries per 16 bytes
+                    for (size_t e = 0; e < d.size(); e += 2) {
+                        float f[4] = {(float)d[e].real(), (float)d[e].imag(), 0.f, 0.f};
+                        if (e + 1 < d.size()) {
+                            f[2] = (float)d[e + 1].real();
+                            f[3] = (float)d[e + 1].imag();
                         }
                         Word16 w;
                         std::memcpy(&w, f, 16);
                         L.tc.push_back(w);
                     }
-                } else if (op.kind == svk::OP_DIAG) {
-                    for (const auto& u : b.mat) {
+                } else {
+                    for (const auto& u : d) {
                         const int64_t re = q62_of(u.real()), im = q62_of(u.imag());
                         Word16 w;
                         std::memcpy(&w.w[0], &re, 8);
                         std::memcpy(&w.w[2], &im, 8);
                         L.tc.push_back(w);
                     }
-                } else if (b.k < 3) {
+                }
+            } else {
+                op.coeff = (int32_t)L.coef.size();
+                L.coef.insert(L.coef.end(), d.begin(), d.end());
+            }
+            L.ops.push_back(op);
+        };
+        auto emit_dense = [&](DevOp op, int k, const std::vector<svp::cd>& M) {
+            op.kind = svk::OP_DENSE;
+            op.k = k;
+            op.flags = 0;
+            if (L.is_tc) {
+                op.coeff = (int32_t)L.tc.size();
+                if (k < 3) {
                     int pos3[3];
                     std::vector<svp::cd> M3;
                     const uint64_t avail = ((1ull << ps.m) - 1);
-                    extend_to3(b.k, op.pos, b.mat, avail, pos3, M3);
+                    extend_to3(k, op.pos, M, avail, pos3, M3);
                     op.k = 3;
                     for (int j = 0; j < 3; j++) op.pos[j] = pos3[j];
                     block_digits(3, M3);
                 } else {
-                    block_digits(b.k, b.mat);
+                    block_digits(k, M);
                 }
             } else {
-                L.coef.insert(L.coef.end(), b.mat.begin(), b.mat.end());
+                op.coeff = (int32_t)L.coef.size();
+                L.coef.insert(L.coef.end(), M.begin(), M.end());
             }
-            if (inject_stall && t05 && op.kind == svk::OP_DENSE) {
+            if (inject_stall && t05) {
                 op.flags |= svk::OPF_TEST_NO_MMA;
                 inject_stall = false;
             }
             L.ops.push_back(op);
-            if (op.kind == svk::OP_DENSE) dp.kmax = std::max(dp.kmax, (int32_t)op.k);
+            dp.kmax = std::max(dp.kmax, (int32_t)op.k);
+        };
+        // permutation: the rows in cycle order, one coefficient element each
+        // holding dst | quarter-phase code << 5 | end-of-cycle << 7 (an exact
+        // small integer in every coefficient format)
+        auto emit_perm = [&](DevOp op, const svp::Block& b) {
+            op.kind = svk::OP_PERM;
+            op.flags = 0;
+            const int D = 1 << b.k;
+            std::vector<int> moves;
+            std::vector<char> seen(D, 0);
+            for (int a0 = 0; a0 < D; a0++) {
+                if (seen[a0]) continue;
+                int a = a0;
+                for (;;) {
+                    seen[a] = 1;
+                    const int nx = b.src[a];
+                    int code = 0;
+                    if (b.quarter) {
+                        const svp::cd v = b.phase[a];
+                        code = v.real() == 1.0 ? 0 : v.imag() == 1.0 ? 1 : v.real() == -1.0 ? 2 : 3;
+                    }
+                    moves.push_back(a | (code << 5) | (nx == a0 ? 128 : 0));
+                    if (nx == a0) break;
+                    a = nx;
+                }
+            }
+            if (L.is_tc) {
+                op.coeff = (int32_t)L.tc.size();
+                for (int v : moves) L.tc.push_back(Word16{{(uint32_t)v, 0u, 0u, 0u}});
+            } else {
+                op.coeff = (int32_t)L.coef.size();
+                for (int v : moves) L.coef.push_back(svp::cd((double)v, 0.0));
+            }
+            L.ops.push_back(op);
+            if (!b.quarter) emit_diag(op, b.phase, false);
+        };
+        for (int bi : ps.blocks) {
+            const svp::Block& b = P.blocks[bi];
+            DevOp op;
+            std::memset(&op, 0, sizeof(op));
+            op.k = b.k;
+            for (int j = 0; j < b.k; j++) {
+                op.pos[j] = pos_of[b.qubits[j]];
+                op.qbit[j] = b.qubits[j];
+            }
+            if (b.kind == svp::BK_DIAG) {
+                emit_diag(op, b.mat, b.sign_only);
+            } else if (b.kind == svp::BK_PERM) {
+                emit_perm(op, b);
+            } else if (b.kind == svp::BK_KRON && !L.is_tc) {
+                for (int j = 0; j < b.k; j++) {
+                    DevOp o1;
+                    std::memset(&o1, 0, sizeof(o1));
+                    o1.pos[0] = pos_of[b.qubits[j]];
+                    o1.qbit[0] = b.qubits[j];
+                    emit_dense(o1, 1, std::vector<svp::cd>(b.factors.begin() + 4 * j, b.factors.begin() + 4 * j + 4));
+                }
+            } else {
+                emit_dense(op, b.k, b.mat);
+            }
         }
         if (dp.kmax < 1) dp.kmax = 1;
         dp.n_ops = (int32_t)(L.ops.size() - dp.op0);
@@ -855,6 +940,148 @@ int sv_set_amplitudes(sv_state* s, const void* in, size_t bytes, int in_is_devic
     s->foreign = true;
     return SV_OK;
 }
+
+// ---- measured autotuner ---------------------------------------------------
+namespace {
+
+// A block of the given class on `qubits`, its matrix formed by the planner
+// from a short gate list: dense = U3 on every qubit, a CZ chain, U3 again;
+// diag = RZZ + RZ (general phases); sign = CZ; perm = a CX chain, a SWAP, X
+// and Y (quarter phases).
+svp::Block calibration_block(int kind, const std::vector<int>& q) {
+    const int k = (int)q.size();
+    std::vector<sv_gate> g;
+    auto add = [&](int op, int q0, int q1, double t, double ph, double la) { g.push_back(sv_gate{op, q0, q1, t, ph, la}); };
+    int bk = svp::BK_DENSE;
+    if (kind == 0) {
+        for (int j = 0; j < k; j++) add(SV_U3, q[j], -1, 0.4 + 0.3 * j, 0.7, -0.2 * j);
+        for (int j = 0; j + 1 < k; j++) add(SV_CZ, q[j], q[j + 1], 0, 0, 0);
+        for (int j = 0; j < k; j++) add(SV_U3, q[j], -1, 1.1 - 0.2 * j, -0.3, 0.5);
+    } else if (kind == 1) {
+        add(SV_RZZ, q[0], q[1], 0.37, 0, 0);
+        add(SV_RZ, q[0], -1, 0.11, 0, 0);
+        bk = svp::BK_DIAG;
+    } else if (kind == 2) {
+        add(SV_CZ, q[0], q[1], 0, 0, 0);
+        bk = svp::BK_DIAG;
+    } else {
+        for (int j = 0; j + 1 < k; j++) add(SV_CX, q[j], q[j + 1], 0, 0, 0);
+        if (k > 1) add(SV_SWAP, q[0], q[k - 1], 0, 0, 0);
+        add(SV_X, q[0], -1, 0, 0, 0);
+        if (k > 1) add(SV_Y, q[1], -1, 0, 0, 0);
+        bk = svp::BK_PERM;
+    }
+    svp::Block b;
+    b.kind = bk;
+    for (int x : q) b.mask |= 1ull << x;
+    b.k = 0;
+    for (int x = 0; x < 64; x++)
+        if ((b.mask >> x) & 1) b.qubits[b.k++] = x;
+    for (size_t t = 0; t < g.size(); t++) b.gates.push_back((int)t);
+    std::vector<svp::Block> v{b};
+    svp::finalize(v, g.data());
+    return v[0];
+}
+
+}  // namespace
+
+extern "C" {
+
+int sv_calibrate(int dt, int arith_req, sv_costs* out) {
+    if (!out || !dt_ok(dt)) return SV_ERR_ARG;
+    const int n = dt == SV_C64 ? 25 : 24;  // 256 MiB: above the L2
+    sv_run_opts o{};
+    o.arith = arith_req;
+    const int arith = resolve_arith(dt, &o, n);
+    sv_state* s = nullptr;
+    int rc = sv_create(n, dt, &s);
+    if (rc) return rc;
+    const int m = std::min(default_tile(dt, arith), max_tile(dt, s->di));
+    const int c = coalesce_of(dt);
+    const double dim = std::ldexp(1.0, n);
+    constexpr int kReps = 8;
+    // kernel time of np passes over the tile qubits 0..m-1, the middle one
+    // applying `mid`; the fastest of three runs
+    auto time_plan = [&](int np, const std::vector<svp::Block>& mid, double* ms) -> int {
+        svp::Plan P;
+        P.n = n;
+        P.fuse_k = svp::kMaxFuse;
+        P.tile_m = m;
+        P.coalesce = c;
+        P.blocks = mid;
+        for (int i = 0; i < np; i++) {
+            svp::Pass ps;
+            ps.local_mask = (1ull << m) - 1;
+            ps.m = m;
+            if (i == np / 2)
+                for (size_t b = 0; b < mid.size(); b++) ps.blocks.push_back((int)b);
+            P.passes.push_back(ps);
+        }
+        double best = 1e300;
+        for (int rep = 0; rep < 3; rep++) {
+            int r = sv_reset(s, 0);
+            if (r == SV_OK) r = apply_plan(s, P, arith, true);
+            if (r != SV_OK) return r;
+            best = std::min(best, s->last.kernel_ms);
+        }
+        *ms = best;
+        return SV_OK;
+    };
+    auto reps_of = [&](int kind, int k) {
+        std::vector<svp::Block> v;
+        for (int r = 0; r < kReps; r++) {  // alternately on the lowest and the highest tile qubits
+            std::vector<int> q;
+            for (int j = 0; j < k; j++) q.push_back((r & 1) ? m - k + j : j);
+            v.push_back(calibration_block(kind, q));
+        }
+        return v;
+    };
+    sv_costs C;
+    std::memset(&C, 0, sizeof(C));
+    C.dt = dt;
+    C.arith = arith;
+    C.n_qubits = n;
+    C.tile_qubits = m;
+    double t2 = 0, t3 = 0, t = 0;
+    const std::vector<svp::Block> none;
+    const double ps_per_ms = 1e9 / dim;  // ms over the whole state -> ps per amplitude
+    auto per_op = [&](double tm) { return std::max(0.0, (tm - t3) * ps_per_ms / kReps); };
+    rc = time_plan(2, none, &t2);
+    if (rc == SV_OK) rc = time_plan(3, none, &t3);
+    if (rc == SV_OK) C.pass_ps = std::max(0.0, (t3 - t2) * ps_per_ms);
+    const int kmax = (dt == SV_C128 && arith == SV_ARITH_TC) ? 4 : 5;
+    for (int k = 1; k <= 5 && rc == SV_OK; k++) {
+        if (k <= kmax) {
+            rc = time_plan(3, reps_of(0, k), &t);
+            if (rc == SV_OK) C.dense_ps[k] = per_op(t);
+        }
+        if (rc == SV_OK) rc = time_plan(3, reps_of(3, k), &t);
+        if (rc == SV_OK) C.perm_ps[k] = per_op(t);
+    }
+    if (rc == SV_OK) rc = time_plan(3, reps_of(1, 2), &t);
+    if (rc == SV_OK) C.diag_ps = per_op(t);
+    if (rc == SV_OK) rc = time_plan(3, reps_of(2, 2), &t);
+    if (rc == SV_OK) C.sign_ps = per_op(t);
+    sv_destroy(s);
+    if (rc == SV_OK) *out = C;
+    return rc;
+}
+
+int sv_set_costs(int dt, int arith, const sv_costs* costs) {
+    if (!dt_ok(dt)) return SV_ERR_ARG;
+    if (arith != SV_ARITH_NATIVE && arith != SV_ARITH_DF64 && arith != SV_ARITH_TC && arith != SV_ARITH_TC_SYNC)
+        return SV_ERR_ARG;
+    std::lock_guard<std::mutex> lk(g_costs_mu);
+    if (!costs) {
+        g_costs.erase({dt, arith});
+        return SV_OK;
+    }
+    if (!(costs->pass_ps >= 0)) return SV_ERR_ARG;
+    g_costs[{dt, arith}] = *costs;
+    return SV_OK;
+}
+
+}  // extern "C"
 
 int sv_norm(sv_state* s, double* out) {
     if (!s || !out) return SV_ERR_ARG;

@@ -6,7 +6,10 @@ namespace svk {
 
 constexpr int kMaxQ = 40;
 
-enum OpKind : int32_t { OP_DENSE = 0, OP_DIAG = 1 };
+// OP_PERM: out[r] = i^code(r) in[src(r)] inside every group of 2^k amplitudes;
+// its coefficient elements list the rows in cycle order (dst | code << 5 |
+// end-of-cycle << 7, exact small integers in every coefficient format).
+enum OpKind : int32_t { OP_DENSE = 0, OP_DIAG = 1, OP_PERM = 2 };
 // OPF_TEST_NO_MMA (tensor-memory mode, tests only): the op issues no MMAs,
 // so its bounded wait runs out and the call reports SV_ERR_TIMEOUT.
 enum OpFlags : int32_t { OPF_SIGN_ONLY = 1, OPF_TEST_NO_MMA = 2 };
@@ -17,7 +20,7 @@ struct alignas(16) DevOp {
     int32_t k;        // qubits of the block (1..5)
     int32_t coeff;    // offset of its coefficients (complex elements)
     int32_t flags;    // OpFlags
-    int32_t pos[5];   // dense: tile positions, ascending; diag: tile position or -1
+    int32_t pos[5];   // dense / perm: tile positions, ascending; diag: tile position or -1
     int32_t qbit[5];  // diag: global qubit of matrix bit j
     int32_t pad[2];
 };

@@ -244,6 +244,85 @@ __device__ __forceinline__ void op_diag(Cx<R>* sm, int m, const DevOp& op, const
 }
 
 // ---------------------------------------------------------------------------
+// Permutation blocks (X, Y, CX, SWAP with diagonal gates whose phases are
+// powers of i): out[r] = i^code(r) in[src(r)] inside every group of 2^k
+// amplitudes, moved along the permutation's cycles with one temporary (each
+// amplitude read once and written once); i^code is a swap of the real and
+// imaginary parts and sign changes, exact in every tile format.  The moves
+// (dst | code << 5 | end-of-cycle << 7, in cycle order) are the op's
+// coefficient elements, decoded by the caller's mv(t).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T rot_i(T v, int code) {  // v * i^code for {re, im} pairs
+    using E = decltype(v.re);
+    const E re = v.re, im = v.im;
+    if (code == 1) return T{-im, re};
+    if (code == 2) return T{-re, -im};
+    if (code == 3) return T{im, -re};
+    return v;
+}
+
+// Groups of a k-qubit op: zero bits inserted at the op's tile positions.
+__device__ __forceinline__ int group_base(int g, const int (&pos)[5], int k) {
+#pragma unroll
+    for (int j = 0; j < 5; j++)
+        if (j < k) g = ((g >> pos[j]) << (pos[j] + 1)) | (g & ((1 << pos[j]) - 1));
+    return g;
+}
+
+// s_mv: the op's moves in cycle order, s_src: per output row r, the row it
+// takes its amplitude from and the phase code (src | code << 5); both staged
+// in shared memory by the caller.  Blocks of up to 3 qubits move a group's
+// 2^k amplitudes through registers (all reads, then all writes); larger
+// blocks follow the cycles with one temporary.
+template <int K, typename S, typename SwzT>
+__device__ __forceinline__ void op_perm(S* sm, int m, const DevOp& op, const int* s_mv, const int* s_src, int tid,
+                                        int nthreads, S (*rot)(S, int)) {
+    constexpr int D = 1 << K;
+    int sp[5], pos[5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) {
+        pos[j] = j < K ? op.pos[j] : 31;
+        sp[j] = j < K ? swz<SwzT>(1 << op.pos[j]) : 0;
+    }
+    auto off = [&](int b) {
+        int o = 0;
+#pragma unroll
+        for (int j = 0; j < K; j++)
+            if ((b >> j) & 1) o ^= sp[j];
+        return o;
+    };
+    const int ng = 1 << (m - K);
+    for (int g = tid; g < ng; g += nthreads) {
+        const int base = swz<SwzT>(group_base(g, pos, K));
+        if constexpr (K <= 3) {
+            S v[D];  // v[r] = the source of output row r (all reads before any write)
+#pragma unroll
+            for (int r = 0; r < D; r++) v[r] = sm[base ^ off(s_src[r] & 31)];
+#pragma unroll
+            for (int r = 0; r < D; r++) sm[base ^ off(r)] = rot(v[r], (s_src[r] >> 5) & 3);
+        } else {
+            for (int t = 0; t < D;) {
+                int mv = s_mv[t];
+                const S first = sm[base ^ off(mv & 31)];
+                for (;;) {
+                    const bool end = (mv & 128) != 0;
+                    const int nx = end ? 0 : s_mv[t + 1];
+                    const S a = end ? first : sm[base ^ off(nx & 31)];
+                    sm[base ^ off(mv & 31)] = rot(a, (mv >> 5) & 3);
+                    t++;
+                    if (end) break;
+                    mv = nx;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ Cx<float> rot_cf(Cx<float> v, int c) { return rot_i(v, c); }
+__device__ __forceinline__ Cx<double> rot_cd(Cx<double> v, int c) { return rot_i(v, c); }
+
+// ---------------------------------------------------------------------------
 // K5-df: tile pass for complex128 states with double-float arithmetic.
 //
 // GB300's FP64 units run about 70x slower than its FP32 units, so complex128
@@ -259,6 +338,12 @@ __device__ __forceinline__ void op_diag(Cx<R>* sm, int m, const DevOp& op, const
 struct alignas(16) DF4 {
     float rh, rl, ih, il;  // re = rh + rl, im = ih + il
 };
+__device__ __forceinline__ DF4 rot_df(DF4 v, int c) {  // v * i^c
+    if (c == 1) return DF4{-v.ih, -v.il, v.rh, v.rl};
+    if (c == 2) return DF4{-v.rh, -v.rl, -v.ih, -v.il};
+    if (c == 3) return DF4{v.ih, v.il, -v.rh, -v.rl};
+    return v;
+}
 
 __device__ __forceinline__ void d2df(double x, float& h, float& l) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -444,6 +529,7 @@ __device__ __forceinline__ void op_diag_df(DF4* sm, int m, const DevOp& op, cons
 struct alignas(16) Q2 {
     long long re, im;
 };
+__device__ __forceinline__ Q2 rot_q(Q2 v, int c) { return rot_i(v, c); }  // exact: |re|, |im| < 2^63
 
 // float64 -> fixed point with FB fraction bits (x * 2^FB truncated toward
 // zero), for |x| < 2^(62 - FB) (components of a normalised state): the
@@ -1353,9 +1439,55 @@ struct TileTraits<MODE_T32> {
     using SwzT = float;
 };
 
+// The move of a permutation op's row t, from its coefficient element.
+__device__ __forceinline__ int perm_move(const Cx<float>* M, int t) { return (int)M[t].re; }
+__device__ __forceinline__ int perm_move(const Cx<double>* M, int t) { return (int)M[t].re; }
+__device__ __forceinline__ int perm_move(const DF4* M, int t) { return (int)M[t].rh; }
+__device__ __forceinline__ int perm_move(const uint4* M, int t) { return (int)M[t].x; }
+__device__ __forceinline__ Cx<float> perm_rot(Cx<float> v, int c) { return rot_cf(v, c); }
+__device__ __forceinline__ Cx<double> perm_rot(Cx<double> v, int c) { return rot_cd(v, c); }
+__device__ __forceinline__ DF4 perm_rot(DF4 v, int c) { return rot_df(v, c); }
+__device__ __forceinline__ Q2 perm_rot(Q2 v, int c) { return rot_q(v, c); }
+
+// Stages a permutation op's moves in shared memory (every thread of the CTA
+// takes part: it holds two CTA barriers) and applies it.
+template <typename S, typename SwzT, typename C>
+__device__ __forceinline__ void apply_perm(S* sm, int m, const DevOp& op, const C* __restrict__ M) {
+    __shared__ int s_mv[32], s_src[32];
+    const int D = 1 << op.k, t = threadIdx.x;
+    __syncthreads();  // the previous op's reads of the tables are done
+    if (t < D) s_mv[t] = perm_move(M, t);
+    __syncthreads();
+    if (t < D) {  // row a_t takes its amplitude from the next row of its cycle
+        const int v = s_mv[t];
+        int nx;
+        if (v & 128) {  // last of its cycle: from the cycle's first row
+            int u = t;
+            while (u > 0 && !(s_mv[u - 1] & 128)) u--;
+            nx = s_mv[u];
+        } else {
+            nx = s_mv[t + 1];
+        }
+        s_src[v & 31] = (nx & 31) | (v & 0x60);
+    }
+    __syncthreads();
+    auto rot = static_cast<S (*)(S, int)>(perm_rot);
+    switch (op.k) {
+        case 1: op_perm<1, S, SwzT>(sm, m, op, s_mv, s_src, t, blockDim.x, rot); break;
+        case 2: op_perm<2, S, SwzT>(sm, m, op, s_mv, s_src, t, blockDim.x, rot); break;
+        case 3: op_perm<3, S, SwzT>(sm, m, op, s_mv, s_src, t, blockDim.x, rot); break;
+        case 4: op_perm<4, S, SwzT>(sm, m, op, s_mv, s_src, t, blockDim.x, rot); break;
+        default: op_perm<5, S, SwzT>(sm, m, op, s_mv, s_src, t, blockDim.x, rot); break;
+    }
+}
+
 template <int MODE, int KMAX>
 __device__ __forceinline__ void apply_op(typename TileTraits<MODE>::Smem* sm, int m, const DevOp& op,
                                          const typename TileTraits<MODE>::Coef* __restrict__ M, uint64_t base) {
+    if (op.kind == OP_PERM) {
+        apply_perm<typename TileTraits<MODE>::Smem, typename TileTraits<MODE>::SwzT>(sm, m, op, M);
+        return;
+    }
     if constexpr (MODE == MODE_TC) {
         if (op.kind == OP_DIAG) {
             op_diag_tc(sm, m, op, reinterpret_cast<const Q2*>(M), base);
@@ -1623,7 +1755,9 @@ __global__ void __launch_bounds__(tile_threads(MODE), MODE == MODE_TC ? 2 : 1)
         for (int o = 0; o < n_ops; o++) {
             const DevOp op = n_ops <= kOpCache ? s_ops[o] : ops[op0 + o];
             if constexpr (MODE == MODE_T05) {
-                if (op.kind == OP_DIAG)
+                if (op.kind == OP_PERM)
+                    apply_perm<Q2, double>(sm, m, op, coef + op.coeff);
+                else if (op.kind == OP_DIAG)
                     op_diag_tc<t05::kLogThreads>(sm, m, op, reinterpret_cast<const Q2*>(coef + op.coeff), base);
                 else {
                     const int* tab = n_ops <= kOpCache ? s_tab + o * t05::kTabInts : nullptr;
@@ -1632,7 +1766,9 @@ __global__ void __launch_bounds__(tile_threads(MODE), MODE == MODE_TC ? 2 : 1)
                 }
                 if (cx.failed) break;  // uniform: decided by a block-wide vote
             } else if constexpr (MODE == MODE_T32) {
-                if (op.kind == OP_DIAG) {
+                if (op.kind == OP_PERM) {
+                    apply_perm<Cx<float>, float>(sm, m, op, coef + op.coeff);
+                } else if (op.kind == OP_DIAG) {
                     if (threadIdx.x < t05::kThreads)  // the issuing warp sits out the 512-thread sweep
                         op_diag<float, t05::kLogThreads>(sm, m, op,
                                                          reinterpret_cast<const Cx<float>*>(coef + op.coeff), base);

@@ -21,6 +21,10 @@ bool gate_is_diagonal(int op) {
     return op == SV_Z || op == SV_S || op == SV_T || op == SV_RZ || op == SV_CZ || op == SV_RZZ;
 }
 
+bool gate_is_monomial(int op) {
+    return gate_is_diagonal(op) || op == SV_X || op == SV_Y || op == SV_CX || op == SV_SWAP;
+}
+
 void gate_matrix(const sv_gate& g, cd* m) {
     const cd I(0, 1);
     const int d = 1 << gate_arity(g.op);
@@ -91,32 +95,62 @@ static void set_qubits(Block& b) {
         if ((b.mask >> q) & 1) b.qubits[b.k++] = q;
 }
 
-std::vector<Block> fuse(int n, const sv_gate* g, size_t ng, int fuse_k) {
+std::vector<Block> fuse(int n, const sv_gate* g, size_t ng, int fuse_k, int keep_monomial, bool pack) {
     std::vector<Block> blocks;
+    std::vector<char> monomial;   // per block: every gate so far is monomial
     std::vector<int> cur(n, -1);  // latest block holding each qubit
     for (size_t t = 0; t < ng; t++) {
         const uint64_t gm = gate_mask(g[t]);
+        const bool mono = gate_is_monomial(g[t].op);
         int bstar = -1;
         for (int q = 0; q < n; q++)
             if ((gm >> q) & 1) bstar = std::max(bstar, cur[q]);
-        if (fuse_k > 1 && bstar >= 0 && popc(blocks[bstar].mask | gm) <= fuse_k) {
-            blocks[bstar].mask |= gm;
-            blocks[bstar].gates.push_back((int)t);
+        // keep_monomial 1: a non-monomial gate stays out of a monomial block;
+        // 2: and a monomial gate out of a block holding another kind
+        auto fits = [&](int b) {
+            return popc(blocks[b].mask | gm) <= fuse_k && !(keep_monomial >= 1 && !mono && monomial[b]) &&
+                   !(keep_monomial >= 2 && mono && !monomial[b]);
+        };
+        int target = -1;
+        if (fuse_k > 1 && bstar >= 0 && fits(bstar)) target = bstar;
+        if (fuse_k > 1 && target < 0 && pack) {
+            // any block at or after bstar may take the gate: every block holding
+            // its qubits comes no later, and none after it holds them; the most
+            // overlapping of the last few blocks wins
+            int best = 1 << 30;
+            for (int b = (int)blocks.size() - 1; b >= std::max(bstar, 0) && b >= (int)blocks.size() - 64; b--) {
+                if (!fits(b)) continue;
+                const int u = popc(blocks[b].mask | gm);
+                if (u < best) {
+                    best = u;
+                    target = b;
+                }
+            }
+        }
+        if (target >= 0) {
+            blocks[target].mask |= gm;
+            blocks[target].gates.push_back((int)t);
+            monomial[target] = monomial[target] && mono;
         } else {
             Block b;
             b.mask = gm;
             b.gates.push_back((int)t);
             blocks.push_back(b);
-            bstar = (int)blocks.size() - 1;
+            monomial.push_back(mono);
+            target = (int)blocks.size() - 1;
         }
         for (int q = 0; q < n; q++)
-            if ((gm >> q) & 1) cur[q] = bstar;
+            if ((gm >> q) & 1) cur[q] = target;
     }
     for (auto& b : blocks) {
         set_qubits(b);
-        bool diag = true;
-        for (int t : b.gates) diag = diag && gate_is_diagonal(g[t].op);
-        b.kind = diag ? BK_DIAG : BK_DENSE;
+        bool diag = true, mono = true, oneq = true;
+        for (int t : b.gates) {
+            diag = diag && gate_is_diagonal(g[t].op);
+            mono = mono && gate_is_monomial(g[t].op);
+            oneq = oneq && gate_arity(g[t].op) == 1;
+        }
+        b.kind = diag ? BK_DIAG : (mono ? BK_PERM : ((oneq && b.k > 1) ? BK_KRON : BK_DENSE));
     }
     return blocks;
 }
@@ -166,9 +200,44 @@ void finalize(std::vector<Block>& blocks, const sv_gate* g) {
                 sign = sign && b.mat[i].imag() == 0.0 && std::fabs(b.mat[i].real()) == 1.0;
             }
             b.sign_only = sign;
-        } else {
-            b.mat.swap(M);
+            continue;
         }
+        if (b.kind == BK_PERM) {
+            // a product of monomial gates keeps one nonzero per row (exact zeros:
+            // every factor's other entries are exact zeros)
+            b.src.assign(D, -1);
+            b.phase.assign(D, cd(0, 0));
+            b.quarter = true;
+            for (int r = 0; r < D; r++) {
+                for (int c = 0; c < D; c++) {
+                    const cd v = M[(size_t)r * D + c];
+                    if (v == cd(0, 0)) continue;
+                    b.src[r] = c;
+                    b.phase[r] = v;
+                }
+                const cd v = b.phase[r];
+                const bool q = (v.imag() == 0.0 && std::fabs(v.real()) == 1.0) ||
+                               (v.real() == 0.0 && std::fabs(v.imag()) == 1.0);
+                b.quarter = b.quarter && q;
+            }
+        }
+        if (b.kind == BK_KRON) {
+            // per qubit, the product of its one-qubit gates in order
+            b.factors.assign((size_t)4 * b.k, cd(0, 0));
+            for (int j = 0; j < b.k; j++) {
+                cd f[4] = {1, 0, 0, 1};
+                for (int t : b.gates) {
+                    if (g[t].q0 != b.qubits[j]) continue;
+                    cd u[4];
+                    gate_matrix(g[t], u);
+                    const cd r[4] = {u[0] * f[0] + u[1] * f[2], u[0] * f[1] + u[1] * f[3],
+                                     u[2] * f[0] + u[3] * f[2], u[2] * f[1] + u[3] * f[3]};
+                    for (int e = 0; e < 4; e++) f[e] = r[e];
+                }
+                for (int e = 0; e < 4; e++) b.factors[(size_t)4 * j + e] = f[e];
+            }
+        }
+        b.mat.swap(M);
     }
 }
 
@@ -255,22 +324,30 @@ std::vector<Pass> schedule(int n, const std::vector<Block>& blocks, int tile_m, 
     return passes;
 }
 
-static double block_flops(const Block& b, double dim) {
+static bool tc_arith(int arith) { return arith == AK_TC || arith == AK_TC32; }
+
+static double block_flops(const Block& b, double dim, int arith) {
     // real flops (FMA = 2) of the block applied to the whole 2^n state
     if (b.kind == BK_DIAG) return b.sign_only ? 0.0 : 6.0 * dim;
+    if (b.kind == BK_PERM) return b.quarter ? 0.0 : 6.0 * dim;  // moves, then a phase pass if not quarter
+    if (b.kind == BK_KRON && !tc_arith(arith)) return 16.0 * (double)b.k * dim;  // k butterflies
     return 8.0 * (double)(1 << b.k) * dim;
 }
 
 // ALU lane instructions per amplitude for one block.
 static double block_instr(const Block& b, int arith) {
     const double D = (double)(1 << b.k);
+    const double cmac = arith == AK_DF64 ? 44.0 : 4.0;  // one complex multiply-add
     if (b.kind == BK_DIAG) {
         if (b.sign_only) return 1.0;
-        return arith == AK_DF64 ? 44.0 : 4.0;
+        return cmac;
     }
+    if (b.kind == BK_PERM) return 2.0 + (b.quarter ? 0.0 : cmac);
     // complex multiply-add: 4 real FMAs; double-float: 4 x (TwoProd + cross
-    // terms + TwoSum) = 44 FP32 instructions
-    return (arith == AK_DF64 ? 44.0 : 4.0) * D;
+    // terms + TwoSum) = 44 FP32 instructions; a Kronecker block is k one-qubit
+    // butterflies (2 multiply-adds per amplitude each)
+    if (b.kind == BK_KRON) return cmac * 2.0 * b.k;
+    return cmac * D;
 }
 
 // Tensor-core modes: 16-bit MMA flops per amplitude of a dense block (digit
@@ -278,13 +355,37 @@ static double block_instr(const Block& b, int arith) {
 // triple split; blocks of fewer than 3 qubits padded to 3) and CUDA-core
 // operations per amplitude (digit split, re-assembly).
 static double tc_mma_flops(const Block& b, int arith) {
-    if (b.kind == BK_DIAG) return 0.0;
+    if (b.kind == BK_DIAG || b.kind == BK_PERM) return 0.0;
     const int k = std::max(3, b.k);
     return (arith == AK_TC32 ? 6.0 : 28.0) * 8.0 * (double)(1 << k);
 }
 static double tc_alu(const Block& b, int arith) {
     if (b.kind == BK_DIAG) return b.sign_only ? 2.0 : (arith == AK_TC32 ? 4.0 : 40.0);
+    if (b.kind == BK_PERM) return 4.0 + (b.quarter ? 0.0 : (arith == AK_TC32 ? 4.0 : 40.0));
     return arith == AK_TC32 ? 30.0 : 150.0;
+}
+
+// Measured cost of one block, picoseconds per amplitude (sv_costs).
+static double measured_ps(const Block& b, int arith, const sv_costs& c) {
+    const bool tc = tc_arith(arith);
+    const int kd = tc ? std::max(3, b.k) : b.k;
+    switch (b.kind) {
+        case BK_DIAG: return b.sign_only ? c.sign_ps : c.diag_ps;
+        case BK_PERM: return c.perm_ps[b.k] + (b.quarter ? 0.0 : c.diag_ps);
+        case BK_KRON: return tc ? c.dense_ps[kd] : b.k * c.dense_ps[1];
+        default: return c.dense_ps[kd];
+    }
+}
+
+// Time of one block over the whole state, without the pass it joins: the
+// measured table, else the analytic terms of model_cost for the block alone.
+static double block_cost(const Block& b, int arith, const Machine& mc, double dim, int amp_bytes) {
+    if (mc.measured) return measured_ps(b, arith, *mc.measured) * 1e-12 * dim;
+    const double rate = arith == AK_FP64 ? mc.fp64_ips : mc.fp32_ips;
+    if (tc_arith(arith))
+        return tc_alu(b, arith) * dim / rate +
+               tc_mma_flops(b, arith) * dim / (arith == AK_TC32 ? mc.tc05_flops : mc.mma_flops);
+    return std::max(block_instr(b, arith) * dim / rate, 2.0 * dim * amp_bytes / mc.smem_Bps);
 }
 
 double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, double* flops, double* alu_ops,
@@ -296,7 +397,7 @@ double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, do
     for (const auto& ps : p.passes) {
         double fl = 0, instr = 0, smem = 0, mma = 0;
         for (int bi : ps.blocks) {
-            fl += block_flops(p.blocks[bi], dim);
+            fl += block_flops(p.blocks[bi], dim, arith);
             if (arith == AK_TC || arith == AK_TC32) {
                 instr += tc_alu(p.blocks[bi], arith) * dim;
                 mma += tc_mma_flops(p.blocks[bi], arith) * dim;
@@ -309,6 +410,12 @@ double model_cost(const Plan& p, int amp_bytes, int arith, const Machine& mc, do
         fl_all += fl;
         ops_all += instr;
         mma_all += mma;
+        if (mc.measured) {  // a pass's measured time: its tile traffic plus each op's
+            double t_ps = mc.measured->pass_ps;
+            for (int bi : ps.blocks) t_ps += measured_ps(p.blocks[bi], arith, *mc.measured);
+            total += t_ps * 1e-12 * dim + mc.launch_s;
+            continue;
+        }
         const double alu = instr / rate + mma / (arith == AK_TC32 ? mc.tc05_flops : mc.mma_flops);
         const double hbm = 2.0 * state / mc.hbm_Bps;
         const double sm = smem / mc.smem_Bps;
@@ -329,21 +436,48 @@ Plan make_plan(int n, const sv_gate* g, size_t ng, int fuse_k, int tile_m, int c
         k_hi = std::min(k_hi, 4);
         k_lo = std::min(k_lo, k_hi);
     }
+    // the tensor-core modes pad blocks below 3 qubits to 3, so narrower
+    // fusion only adds blocks: the autotuner starts at 3 there
+    if (fuse_k == 0 && tc_arith(arith)) k_lo = std::min(3, k_hi);
+    // the autotuner: every fusion width, with and without keeping runs of
+    // monomial gates as permutation blocks, with and without packing gates
+    // on disjoint qubits into one block.  The variants of a width are scored
+    // by their blocks' cost alone and only the cheapest is scheduled into
+    // passes (scheduling is most of the planning time), then the widths are
+    // compared by the full cost model.
+    const double dim = std::ldexp(1.0, n);
     for (int k = k_lo; k <= k_hi; k++) {
+        std::vector<Block> chosen;
+        double chosen_cost = 1e300;
+        for (int variant = 0; variant < (k > 1 ? 6 : 1); variant++) {
+            const int keep = variant % 3;
+            const bool pack = variant >= 3;
+            std::vector<Block> blocks = fuse(n, g, ng, k, keep, pack);
+            // known before the matrices are formed: diagonal blocks made of CZ / Z
+            // gates only are sign flips; permutation blocks without T / RZ / RZZ
+            // have quarter phases
+            for (auto& b : blocks) {
+                bool sign = true, quarter = true;
+                for (int t : b.gates) {
+                    sign = sign && (g[t].op == SV_CZ || g[t].op == SV_Z);
+                    quarter = quarter && g[t].op != SV_T && g[t].op != SV_RZ && g[t].op != SV_RZZ;
+                }
+                if (b.kind == BK_DIAG) b.sign_only = sign;
+                if (b.kind == BK_PERM) b.quarter = quarter;
+            }
+            double cost = 0;
+            for (const auto& b : blocks) cost += block_cost(b, arith, mc, dim, amp_bytes);
+            if (cost < chosen_cost) {
+                chosen_cost = cost;
+                chosen.swap(blocks);
+            }
+        }
         Plan p;
         p.n = n;
         p.fuse_k = k;
         p.tile_m = std::min(tile_m, n);
         p.coalesce = std::min(coalesce, n);
-        p.blocks = fuse(n, g, ng, k);
-        // sign_only is known before the matrices are formed: diagonal blocks
-        // made of CZ / Z gates only
-        for (auto& b : p.blocks) {
-            if (b.kind != BK_DIAG) continue;
-            bool s = true;
-            for (int t : b.gates) s = s && (g[t].op == SV_CZ || g[t].op == SV_Z);
-            b.sign_only = s;
-        }
+        p.blocks.swap(chosen);
         p.passes = schedule(n, p.blocks, p.tile_m, p.coalesce);
         double fl = 0;
         p.model_s = model_cost(p, amp_bytes, arith, mc, &fl);
@@ -370,7 +504,7 @@ int check_plan(const Plan& p, size_t ng, const sv_gate* g) {
             used[bi] = 1;
             const Block& b = p.blocks[bi];
             if (b.k < 1 || b.k > kMaxFuse) return 3;
-            if (b.kind == BK_DENSE && (b.mask & ~ps.local_mask)) return 4;
+            if (b.kind != BK_DIAG && (b.mask & ~ps.local_mask)) return 4;
             for (int t : b.gates) {
                 if (t < 0 || (size_t)t >= ng || seen[t]) return 5;
                 seen[t] = 1;

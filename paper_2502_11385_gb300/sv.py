@@ -23,6 +23,8 @@ SV_OK, SV_ERR_ARG, SV_ERR_QUBIT, SV_ERR_OOM, SV_ERR_SIZE, SV_ERR_CUDA, SV_ERR_TI
     0, -1, -2, -3, -4, -5, -6, -7
 C64, C128 = 0, 1
 ARITH_AUTO, ARITH_NATIVE, ARITH_DF64, ARITH_TC, ARITH_TC_SYNC = 0, 1, 2, 3, 4
+# block classes of a plan (sv_plan.h)
+BLOCK_DENSE, BLOCK_DIAG, BLOCK_PERM, BLOCK_KRON = 0, 1, 2, 3
 DTYPES = {"c64": C64, "c128": C128, C64: C64, C128: C128}
 NP_DTYPE = {C64: np.complex64, C128: np.complex128}
 
@@ -59,6 +61,12 @@ class BatchInfo(ctypes.Structure):
 class PlanSummary(ctypes.Structure):
     _fields_ = [("n_blocks", ctypes.c_int32), ("n_passes", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
                 ("tile_qubits", ctypes.c_int32), ("flops", ctypes.c_double), ("model_ms", ctypes.c_double)]
+
+
+class Costs(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_int32), ("arith", ctypes.c_int32), ("n_qubits", ctypes.c_int32),
+                ("tile_qubits", ctypes.c_int32), ("pass_ps", ctypes.c_double), ("dense_ps", ctypes.c_double * 6),
+                ("diag_ps", ctypes.c_double), ("sign_ps", ctypes.c_double), ("perm_ps", ctypes.c_double * 6)]
 
 
 _vp, _sz, _i32, _u64, _dp = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
@@ -103,6 +111,8 @@ _SIGS = {
                        ctypes.POINTER(_i32), ctypes.POINTER(_i32), _sz, ctypes.POINTER(ctypes.c_double), _sz], _i32),
     "sv_plan_pass": ([_vp, _i32, ctypes.POINTER(_u64), ctypes.POINTER(_i32), ctypes.POINTER(_i32), _sz], _i32),
     "sv_plan_check": ([_vp, _vp, _sz], _i32),
+    "sv_calibrate": ([_i32, _i32, ctypes.POINTER(Costs)], _i32),
+    "sv_set_costs": ([_i32, _i32, ctypes.POINTER(Costs)], _i32),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -129,6 +139,38 @@ def version() -> str:
 def _check(code, what):
     if code != SV_OK:
         raise SvError(code, what)
+
+
+_COST_KEYS = ("pass_ps", "dense_ps", "diag_ps", "sign_ps", "perm_ps")
+
+
+def calibrate(dtype, arith=ARITH_AUTO) -> dict:
+    """Measures the tile-pass cost table on the current device (sv_calibrate):
+    picoseconds per amplitude of a pass, of dense / permutation blocks of
+    k = 1..5 qubits and of diagonal blocks.  The returned dict carries the
+    resolved arithmetic it was measured for."""
+    c = Costs()
+    _check(_lib.sv_calibrate(DTYPES[dtype], int(arith), ctypes.byref(c)), "sv_calibrate")
+    return {"dt": c.dt, "arith": c.arith, "n_qubits": c.n_qubits, "tile_qubits": c.tile_qubits,
+            "pass_ps": c.pass_ps, "dense_ps": list(c.dense_ps), "diag_ps": c.diag_ps, "sign_ps": c.sign_ps,
+            "perm_ps": list(c.perm_ps)}
+
+
+def set_costs(dtype, arith: int, costs) -> None:
+    """Installs a measured cost table for (dtype, resolved arith) in the
+    planner (sv_set_costs); costs=None returns that pair to the analytic
+    model."""
+    if costs is None:
+        _check(_lib.sv_set_costs(DTYPES[dtype], int(arith), None), "sv_set_costs")
+        return
+    c = Costs()
+    c.dt, c.arith = DTYPES[dtype], int(arith)
+    c.n_qubits, c.tile_qubits = int(costs.get("n_qubits", 0)), int(costs.get("tile_qubits", 0))
+    c.pass_ps, c.diag_ps, c.sign_ps = float(costs["pass_ps"]), float(costs["diag_ps"]), float(costs["sign_ps"])
+    for i in range(6):
+        c.dense_ps[i] = float(costs["dense_ps"][i])
+        c.perm_ps[i] = float(costs["perm_ps"][i])
+    _check(_lib.sv_set_costs(c.dt, c.arith, ctypes.byref(c)), "sv_set_costs")
 
 
 def state_bytes(n: int, dtype) -> int:
@@ -454,12 +496,13 @@ class Plan:
                                   None, 0, None, 0), "sv_plan_block")
         ids = (_i32 * max(ng.value, 1))()
         d = 1 << k.value
-        nm = d * d if kind.value == 0 else d
+        diag = kind.value == BLOCK_DIAG
+        nm = d if diag else d * d
         mat = (ctypes.c_double * (2 * nm))()
         _check(_lib.sv_plan_block(self._h, b, None, None, None, None, ids, ng.value, mat, 2 * nm), "sv_plan_block")
         m = np.frombuffer(mat, dtype=np.float64).copy().view(np.complex128)
         return {"kind": kind.value, "k": k.value, "qubits": list(qs)[: k.value],
-                "gates": list(ids)[: ng.value], "mat": m.reshape(d, d) if kind.value == 0 else m}
+                "gates": list(ids)[: ng.value], "mat": m if diag else m.reshape(d, d)}
 
     def pass_info(self, i: int) -> dict:
         mask, nb = _u64(), _i32()

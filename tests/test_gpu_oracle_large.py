@@ -134,3 +134,30 @@ def test_family_against_oracle(sv, family, dtype):
         mx, rel = _compare(got, ref)
         print(f"{family} {n}q {dtype} arith={arith}: max|da|={mx:.3e} rel L2={rel:.3e}")
         assert mx <= TOL[dtype], (family, dtype, arith, mx)
+
+
+def test_measured_autotuner_tables_and_parity(sv):
+    """sv_calibrate on this GPU: every table is positive where defined, a
+    pass costs at least the HBM sweep of a 16- or 8-byte amplitude at 8 TB/s,
+    and circuits planned with the installed tables still match the oracle."""
+    from paper_2502_11385_gb300 import tune
+    try:
+        used = tune.ensure(path=os.path.join(os.path.dirname(tune.CACHE), "autotune_test.json"), force=True)
+        assert len(used) == len(tune.MODES)
+        for key, t in used.items():
+            amp = 16 if "|c128|" in key else 8
+            assert t["pass_ps"] >= 2 * amp / 8e12 * 1e12, (key, t["pass_ps"])
+            kmax = 4 if ("|c128|" in key and t["arith"] == sv.ARITH_TC) else 5
+            assert all(t["dense_ps"][k] > 0 for k in range(1, kmax + 1)), (key, t)
+            assert all(t["perm_ps"][k] > 0 for k in range(1, 6)) and t["diag_ps"] > 0 and t["sign_ps"] > 0
+            print(key, {k: (round(v, 2) if isinstance(v, float) else [round(x, 2) for x in v])
+                        for k, v in t.items() if k.endswith("_ps")})
+        for n, dtype in ((18, "c128"), (22, "c128"), (18, "c64"), (24, "c64")):
+            g = _random_circuit(n, 80, 900 + n)
+            with sv.State(n, dtype) as s:
+                s.apply_circuit(g)
+                got = s.amplitudes()
+            mx, _ = _compare(got, oracle.run(n, g))
+            assert mx <= TOL[dtype], (n, dtype, mx)
+    finally:
+        tune.clear()

@@ -639,3 +639,49 @@ def test_tc32_accuracy_matches_float32(sv):
         errs[arith] = (np.linalg.norm(amp - ref) / np.linalg.norm(ref), np.abs(amp - ref).max())
     assert errs[sv.ARITH_TC][1] <= 1e-6, errs
     assert errs[sv.ARITH_TC][0] <= 8 * max(errs[sv.ARITH_NATIVE][0], 1e-7), errs
+
+
+# ---------------------------------------------------------------------------
+# Block classes: permutation blocks (amplitude moves with quarter phases, or
+# a move then a diagonal pass for T / RZ / RZZ phases) and Kronecker blocks
+# (one butterfly per qubit outside the tensor-core modes)
+# ---------------------------------------------------------------------------
+ALL_MODES = [("c128", 0), ("c128", 1), ("c128", 2), ("c128", 3), ("c128", 4), ("c64", 1), ("c64", 3)]
+
+
+def _perm_network(n, count, seed):
+    """CX / SWAP / X / Y / Z / S / T / CZ / RZZ networks with a few H and U3
+    gates between them."""
+    rng = np.random.default_rng(seed)
+    ops = [W.CX, W.CX, W.SWAP, W.X, W.Y, W.Z, W.S, W.T, W.CZ, W.RZZ]
+    rows = []
+    for i in range(count):
+        op = ops[int(rng.integers(0, len(ops)))] if i % 9 else [W.H, W.U3][int(rng.integers(0, 2))]
+        q0 = int(rng.integers(0, n))
+        q1 = int(rng.choice([q for q in range(n) if q != q0])) if op >= W.CX else -1
+        rows.append((op, q0, q1, *rng.uniform(-4, 4, 3)))
+    return W.gates(rows)
+
+
+@pytest.mark.parametrize("dtype,arith", ALL_MODES)
+@pytest.mark.parametrize("n,tile", [(10, 0), (16, 10), (20, 0)])
+def test_permutation_blocks_every_mode(sv, n, tile, dtype, arith):
+    g = _perm_network(n, 160, 300 + n)
+    p = sv.Plan(n, dtype, g, sv.run_opts(arith=arith, tile_qubits=tile))
+    kinds = {p.block(b)["kind"] for b in range(p.summary()["n_blocks"])}
+    assert sv.BLOCK_PERM in kinds
+    _check(sv, n, dtype, g, arith=arith, tile_qubits=tile)
+
+
+@pytest.mark.parametrize("dtype,arith", ALL_MODES)
+def test_kronecker_layers_every_mode(sv, dtype, arith):
+    """Layers of one-qubit rotations on every qubit between CZ layers."""
+    n = 14
+    rows = []
+    for layer in range(6):
+        rows += [(W.U3, q, -1, 0.3 * q + layer, 0.2 * layer, -0.1 * q) for q in range(n)]
+        rows += [(W.RX, q, -1, 0.5 + 0.1 * q) for q in range(n)]
+        rows += [(W.CZ, q, q + 1) for q in range(layer % 2, n - 1, 2)]
+    g = W.gates(rows)
+    _check(sv, n, dtype, g, arith=arith)
+    _check(sv, n, dtype, g, arith=arith, tile_qubits=10)

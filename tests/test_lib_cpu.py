@@ -77,7 +77,7 @@ def _plan_unitary_state(sv, plan, n):
     for i in range(nb):
         for b in plan.pass_info(i)["blocks"]:
             blk = plan.block(b)
-            m = blk["mat"] if blk["kind"] == 0 else np.diag(blk["mat"])
+            m = np.diag(blk["mat"]) if blk["kind"] == sv.BLOCK_DIAG else blk["mat"]
             psi = dense.embed(n, m, blk["qubits"]) @ psi
     return psi
 
@@ -109,7 +109,7 @@ def test_plan_multi_pass_locality(sv):
         assert pi["local_mask"] & 0b11111 == 0b11111      # coalescing qubits always local
         for b in pi["blocks"]:
             blk = p.block(b)
-            if blk["kind"] == 0:
+            if blk["kind"] != sv.BLOCK_DIAG:
                 assert all((pi["local_mask"] >> q) & 1 for q in blk["qubits"])
 
 
@@ -129,7 +129,7 @@ def test_fused_block_matrix_is_product_of_oracle_gates(sv):
             gq = [int(r["q0"])] + ([int(r["q1"])] if op >= W.CX else [])
             # embed into the block's local space (bit j = qs[j]) via the dense helper
             ref = dense.embed(len(qs), u, [qs.index(q) for q in gq]) @ ref
-        m = blk["mat"] if blk["kind"] == 0 else np.diag(blk["mat"])
+        m = np.diag(blk["mat"]) if blk["kind"] == sv.BLOCK_DIAG else blk["mat"]
         assert np.abs(m - ref).max() < 1e-13
 
 
@@ -158,3 +158,110 @@ def test_autotuned_plan_is_valid_for_workloads(sv):
         assert p.check() == 0, (n, dt)
         s = p.summary()
         assert s["n_passes"] >= 1 and 1 <= s["fuse_k"] <= 5
+
+
+def test_permutation_blocks_classified(sv):
+    """Runs of X / Y / CX / SWAP with diagonal gates fuse into permutation
+    blocks: one nonzero per row, of modulus 1 (the GHZ chain, a SWAP network,
+    Paulis and S / T phases); the plan still reproduces the circuit."""
+    n = 8
+    rows = [(W.CX, q, q + 1) for q in range(n - 1)]
+    rows += [(W.SWAP, 0, 5), (W.X, 3, -1), (W.Y, 6, -1), (W.S, 2, -1), (W.T, 7, -1), (W.CX, 7, 1), (W.CZ, 4, 6)]
+    g = W.gates(rows)
+    p = sv.Plan(n, "c128", g, sv.run_opts(max_fuse_k=4))
+    assert p.check() == 0
+    kinds = set()
+    for b in range(p.summary()["n_blocks"]):
+        blk = p.block(b)
+        kinds.add(blk["kind"])
+        if blk["kind"] == sv.BLOCK_PERM:
+            m = blk["mat"]
+            nz = np.abs(m) > 0
+            assert (nz.sum(axis=0) == 1).all() and (nz.sum(axis=1) == 1).all()
+            assert np.allclose(np.abs(m[nz]), 1.0, atol=1e-15)
+    assert kinds <= {sv.BLOCK_PERM, sv.BLOCK_DIAG} and sv.BLOCK_PERM in kinds
+    assert np.abs(_plan_unitary_state(sv, p, n) - oracle.run(n, g)).max() < 1e-14
+
+
+def test_kronecker_blocks_are_tensor_products(sv):
+    """A layer of one-qubit gates on disjoint qubits packs into Kronecker
+    blocks whose matrix is the tensor product of the per-qubit products (bit
+    j of the block index is its j-th qubit, so the last qubit's factor comes
+    first in numpy's kron)."""
+    n = 8
+    rows = [(W.U3, q, -1, 0.3 + q, 0.1 * q, -0.7) for q in range(n)]
+    rows += [(W.RY, q, -1, 0.2 * q) for q in range(n)]
+    g = W.gates(rows)
+    p = sv.Plan(n, "c64", g, sv.run_opts(max_fuse_k=4))
+    assert p.check() == 0
+    found = 0
+    for b in range(p.summary()["n_blocks"]):
+        blk = p.block(b)
+        if blk["kind"] != sv.BLOCK_KRON:
+            continue
+        found += 1
+        ref = np.ones((1, 1), dtype=complex)
+        for q in blk["qubits"]:
+            f = np.eye(2, dtype=complex)
+            for t in blk["gates"]:
+                r = g[t]
+                if int(r["q0"]) == q:
+                    f = oracle.gate_matrix(int(r["op"]), r["theta"], r["phi"], r["lam"]) @ f
+            ref = np.kron(f, ref)
+        assert np.abs(blk["mat"] - ref).max() < 1e-14
+    assert found >= 1
+    assert np.abs(_plan_unitary_state(sv, p, n) - oracle.run(n, g)).max() < 1e-14
+
+
+def _table(**over):
+    t = {"pass_ps": 5.0, "dense_ps": [0, 1.0, 2.0, 3.0, 4.0, 5.0], "diag_ps": 0.5, "sign_ps": 0.2,
+         "perm_ps": [0, 0.1, 0.1, 0.1, 0.1, 0.1]}
+    t.update(over)
+    return t
+
+
+def test_installed_costs_steer_the_planner(sv):
+    """A measured table replaces the analytic model for its (dtype, arith)
+    pair: with wide blocks priced out the planner fuses at most 2 qubits, with
+    passes priced out it takes the widest blocks; removing the table restores
+    the analytic choice.  Every plan keeps its invariants."""
+    n = 16
+    g = W.concat(W.ghz_prefix(n), W.brickwork(n, 6, 4))
+    o = sv.run_opts(arith=sv.ARITH_NATIVE)
+    base = sv.Plan(n, "c64", g, o).summary()
+    try:
+        sv.set_costs("c64", sv.ARITH_NATIVE, _table(dense_ps=[0, 1.0, 2.0, 500.0, 900.0, 1900.0]))
+        p = sv.Plan(n, "c64", g, o)
+        assert p.summary()["fuse_k"] <= 2 and p.check() == 0
+        sv.set_costs("c64", sv.ARITH_NATIVE, _table(pass_ps=1e4, dense_ps=[0, 1.0, 1.0, 1.0, 1.0, 1.0]))
+        p = sv.Plan(n, "c64", g, o)
+        assert p.summary()["fuse_k"] == 5 and p.check() == 0
+        # a table for another pair leaves this one alone
+        sv.set_costs("c64", sv.ARITH_NATIVE, None)
+        sv.set_costs("c128", sv.ARITH_DF64, _table(pass_ps=1e4))
+        assert sv.Plan(n, "c64", g, o).summary() == base
+    finally:
+        sv.set_costs("c64", sv.ARITH_NATIVE, None)
+        sv.set_costs("c128", sv.ARITH_DF64, None)
+    with pytest.raises(sv.SvError):
+        sv.set_costs("c64", sv.ARITH_AUTO, _table())
+
+
+def test_autotune_cache_round_trip(sv, tmp_path):
+    """The JSON cache keeps one table per (GPU, kernel build, dtype, arith);
+    install() picks the entries of this GPU and build only."""
+    from paper_2502_11385_gb300 import tune
+    path = str(tmp_path / "autotune.json")
+    kern = tune.kernel_key()
+    t = _table()
+    t["arith"] = sv.ARITH_NATIVE
+    table = {tune.entry_key("GPU-A", kern, "c64", sv.ARITH_NATIVE): t,
+             tune.entry_key("GPU-B", kern, "c128", sv.ARITH_TC): dict(t, arith=sv.ARITH_TC)}
+    tune.save(table, path)
+    back = tune.load(path)
+    assert back == table
+    try:
+        assert tune.install(back, "GPU-A", kern) == 1
+        assert tune.install(back, "GPU-A", "other-build") == 0
+    finally:
+        tune.clear()
