@@ -685,3 +685,19 @@ def test_kronecker_layers_every_mode(sv, dtype, arith):
     g = W.gates(rows)
     _check(sv, n, dtype, g, arith=arith)
     _check(sv, n, dtype, g, arith=arith, tile_qubits=10)
+
+
+def test_sharded_local_applier_is_the_library(sv):
+    """The sharded state's default local applier runs a rank's gate segment
+    through the CUDA library on its chunk in place (a GPU rank of a sharded
+    run; the exchanges between ranks are tested on CPU ranks)."""
+    import torch
+    from paper_2502_11385_gb300 import shard
+    n = 14
+    g = _random_circuit(n, 90, 4242)
+    for dtype, ct in (("c128", torch.complex128), ("c64", torch.complex64)):
+        chunk = torch.zeros(1 << n, dtype=ct, device="cuda")
+        chunk[0] = 1
+        shard._library_apply(chunk, n, g)
+        torch.cuda.synchronize()
+        assert np.abs(chunk.cpu().numpy().astype(np.complex128) - oracle.run(n, g)).max() <= TOL[dtype]
