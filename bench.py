@@ -456,12 +456,35 @@ def batch_summary(steps):
         loop_ms = (time.perf_counter() - t0) * 1e3 / steps
         same = all(torch.equal(a, c) for a, c in zip(ref, outs))
         h.close()
-        del bufs, outs, ref
-        torch.cuda.empty_cache()
         nv = len(gl)
         res[dtype] = {"batched_variants_per_s": round(nv / batch_ms * 1e3, 1),
                       "looped_variants_per_s": round(nv / loop_ms * 1e3, 1),
                       "speedup": round(loop_ms / batch_ms, 3), "bitwise_equal": same, "sweeps": steps}
+        if dtype == "c128":
+            # reconstruction (Eqs. 3.2-3.7) of the marginal over 12 upstream and 12
+            # downstream qubits (2^24 outputs; the 2^40 joint does not fit)
+            cut_q = list(cc.cut_qubits)
+            keep_a = sum(1 << q for q in [q for q in range(cc.width_a) if q not in cut_q][:12])
+            rec = torch.empty(1 << 24, dtype=torch.float64, device="cuda")
+            up_o, dn_o = outs[:len(ups)], outs[len(ups):]
+            sv.cut_reconstruct(up_o, dn_o, cc.width_a, cut_q, cc.width_b, keep_a, (1 << 12) - 1, out=rec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                sv.cut_reconstruct(up_o, dn_o, cc.width_a, cut_q, cc.width_b, keep_a, (1 << 12) - 1, out=rec)
+            torch.cuda.synchronize()
+            rec_ms = (time.perf_counter() - t0) * 1e3 / steps
+            rec_bytes = (len(ups) * (1 << cc.width_a) + len(downs) * (1 << cc.width_b) + (1 << 24)) * 8
+            peak = load_peaks()[0]["hbm_gbs"]
+            res["reconstruction"] = {"outputs": "2^24 (12 upstream + 12 downstream qubits)",
+                                     "terms": 4 ** len(cut_q), "ms": round(rec_ms, 3),
+                                     "algorithmic_bytes": rec_bytes,
+                                     "gbs": round(rec_bytes / rec_ms / 1e6, 1),
+                                     "frac_of_hbm": round(rec_bytes / rec_ms / 1e6 / peak, 4),
+                                     "abs_sum_minus_1": abs(rec.sum().item() - 1.0)}
+            del rec
+        del bufs, outs, ref
+        torch.cuda.empty_cache()
     return res
 
 

@@ -398,6 +398,31 @@ def test_cut_reconstruction_on_gpu(sv, n, depth, cut_lo, k, switch):
     assert np.abs(part - oracle.marginal(oracle.run(n, cc.full), gmask)).max() <= 1e-12
 
 
+@pytest.mark.parametrize("n,depth,cut_lo,k,switch", [(14, 6, 5, 4, 3), (16, 8, 6, 4, 4)])
+def test_cut_reconstruction_four_cuts_and_partial_masks(sv, n, depth, cut_lo, k, switch):
+    """K = 4 (256 term codes, several chunks of the contraction), the full
+    distribution and marginals over several kept qubits on both sides against
+    the uncut oracle."""
+    import torch
+    cc = W.cuttable_brickwork(n, depth, 300 + n, cut_lo=cut_lo, n_cuts=k, switch_layer=switch)
+    ups, downs = cc.upstream_variants(), cc.downstream_variants()
+    up_t = [torch.empty(1 << cc.width_a, dtype=torch.float64, device="cuda") for _ in ups]
+    dn_t = [torch.empty(1 << cc.width_b, dtype=torch.float64, device="cuda") for _ in downs]
+    items = [(cc.width_a, "c128", g, t) for g, t in zip(ups, up_t)] + \
+            [(cc.width_b, "c128", g, t) for g, t in zip(downs, dn_t)]
+    _, status = sv.batch_run(items)
+    assert all(s == 0 for s in status)
+    psi = oracle.run(n, cc.full)
+    rec = sv.cut_reconstruct(up_t, dn_t, cc.width_a, list(cc.cut_qubits), cc.width_b)
+    assert np.abs(rec - oracle.probabilities(psi)).max() <= 1e-12
+    eff_a = [q for q in range(cc.width_a) if q not in cc.cut_qubits]  # upstream qubit eff_a[i] = global i
+    for ka, kb in ((0b1011, 0b1), (0b1, 0b110010), ((1 << len(eff_a)) - 1, 0b1)):
+        mask_a = sum(1 << eff_a[i] for i in range(len(eff_a)) if (ka >> i) & 1)
+        part = sv.cut_reconstruct(up_t, dn_t, cc.width_a, list(cc.cut_qubits), cc.width_b, mask_a, kb)
+        gmask = ka | (kb << len(eff_a))
+        assert np.abs(part - oracle.marginal(psi, gmask)).max() <= 1e-12, (ka, kb)
+
+
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_cut_variants_shared_work_matches_plain(sv, dtype):
     """Variant shortcuts (shared upstream body, downstream by linearity) give
