@@ -511,6 +511,71 @@ def serve_summary(count):
     return res
 
 
+def dtype_summary(gates, n, dtype, steps):
+    """The same circuit in another dtype, for the default line: tile-pass
+    kernel time per circuit (CUDA events on the handle's stream) and the tile
+    pass's HBM roofline fraction."""
+    import torch
+    from paper_2502_11385_gb300 import sv
+    ct = torch.complex64 if dtype == "c64" else torch.complex128
+    buf = torch.empty(1 << n, dtype=ct, device="cuda")
+    stream = torch.cuda.Stream()
+    st = sv.State.from_tensor(buf, n, dtype, stream=stream.cuda_stream)
+    opts = sv.run_opts(timing=1)
+    ks = []
+    for i in range(steps + 2):
+        st.reset(0)
+        st.apply_circuit(gates, opts)
+        if i >= 2:
+            ks.append(st.stats())
+    st.close()
+    del buf
+    torch.cuda.empty_cache()
+    s0 = ks[-1]
+    kern_ms = statistics.mean(k["kernel_ms"] for k in ks)
+    amp = 8 if dtype == "c64" else 16
+    launch_gbs = 2 * (amp << n) / (kern_ms / s0["n_launches"] / 1e3) / 1e9
+    peak = load_peaks()[0]["hbm_gbs"]
+    return {"kernel_ms_per_circuit": round(kern_ms, 2), "passes": s0["n_passes"], "blocks": s0["n_blocks"],
+            "fuse_k": s0["fuse_k"], "tile_pass_gbs": round(launch_gbs, 1),
+            "frac_of_measured_hbm": round(launch_gbs / peak, 4)}
+
+
+def precision_summary(n=32):
+    """The precision form (QAOA p = 2 on a seeded 3-regular graph): the
+    circuit in complex128 and in complex64, their kernel times, and the
+    complex64 result's max |delta a| and probability L1 distance from the
+    complex128 one (both probability vectors computed in float64)."""
+    import torch
+    from paper_2502_11385_gb300 import sv, workloads as W
+    free = torch.cuda.mem_get_info()[0]
+    if free < (1 << n) * (16 + 8 + 8 + 8) * 1.1:
+        return {"skipped": f"needs {(1 << n) * 40 / 2**30:.0f} GiB of free device memory"}
+    g = W.workload_qaoa(n, 2, 3)[0]
+    res = {"workload": f"{n}q QAOA p=2 seed 3 on a random 3-regular graph ({len(g)} gates)"}
+    bufs = {}
+    for dtype, ct in (("c128", torch.complex128), ("c64", torch.complex64)):
+        buf = torch.empty(1 << n, dtype=ct, device="cuda")
+        st = sv.State.from_tensor(buf, n, dtype)
+        st.reset(0)
+        st.apply_circuit(g, sv.run_opts(timing=1))
+        res[f"{dtype}_kernel_ms"] = round(st.stats()["kernel_ms"], 1)
+        res[f"{dtype}_norm_minus_1"] = abs(st.norm() - 1.0)
+        st.close()
+        bufs[dtype] = buf
+    a, b = bufs["c128"], bufs["c64"]
+    chunk, mx, l1 = 1 << 26, 0.0, 0.0
+    for i in range(0, 1 << n, chunk):
+        x, y = a[i:i + chunk], b[i:i + chunk].to(torch.complex128)
+        mx = max(mx, (x - y).abs().max().item())
+        l1 += ((x.real ** 2 + x.imag ** 2) - (y.real ** 2 + y.imag ** 2)).abs().sum().item()
+    res["c64_vs_c128_max_abs_da"] = mx
+    res["c64_vs_c128_prob_l1"] = l1
+    del bufs, a, b
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_serve_form(args):
     import torch
     import __graft_entry__
@@ -731,7 +796,11 @@ def main():
     del buf, probs, host_p
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_forms:
-        # the batching and serving forms, measured after the timed region
+        # the other dtype, the precision form and the batching and serving
+        # forms, measured after the timed region
+        other = "c64" if dt == "c128" else "c128"
+        out[other] = dtype_summary(gates, n, other, max(2, min(args.steps, 5)))
+        out["precision"] = precision_summary()
         out["batch"] = batch_summary(max(2, min(args.steps, 5)))
         out["serve"] = serve_summary(args.serve_sample)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
