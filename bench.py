@@ -506,7 +506,8 @@ def serve_summary(count):
         _, st = serve.Server(opts=opts, keep_outputs=False).run(reqs)
         _, ss = serve.run_serial(reqs, opts, keep_outputs=False)
         res[f"rho_{rho}"] = {"served": {k: st[k] for k in ("circuits_per_s", "p50_ms", "p99_ms", "mean_batch")},
-                             "serial": {k: ss[k] for k in ("circuits_per_s", "p50_ms", "p99_ms")},
+                             "serial": {k: ss[k] for k in ("circuits_per_s", "p50_ms", "p99_ms",
+                                                           "tile_pass_gpu_s", "throughput_bound_small_hidden")},
                              "throughput_ratio": round(st["circuits_per_s"] / ss["circuits_per_s"], 3)}
     return res
 

@@ -211,12 +211,20 @@ class Server:
         return results, st
 
 
-def run_serial(requests, opts=None, time_scale=1.0, keep_outputs=True):
-    """The plain single-circuit path, one request at a time in arrival order."""
+def run_serial(requests, opts=None, time_scale=1.0, keep_outputs=True, large_qubits=24):
+    """The plain single-circuit path, one request at a time in arrival order.
+    Also records each request's tile-pass GPU time (CUDA events), split
+    between requests below and from `large_qubits` on: with the small ones
+    fully hidden, no schedule can serve the stream faster than
+    requests / (GPU time of the large ones)."""
     import torch
     results = [Result(q.rid, q.n, q.dtype, q.arrival * time_scale) for q in requests]
     stream = torch.cuda.Stream()
     handle = None
+    o = opts if opts is not None else sv.run_opts()
+    topts = sv.run_opts(max_fuse_k=o.max_fuse_k, tile_qubits=o.tile_qubits, arith=o.arith,
+                        debug_checks=o.debug_checks, timing=1)
+    gpu_ms = {"small": 0.0, "large": 0.0}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for q, r in zip(requests, results):
@@ -232,7 +240,8 @@ def run_serial(requests, opts=None, time_scale=1.0, keep_outputs=True):
         else:
             handle.rebind(buf, q.n, q.dtype)
         handle.reset(0)
-        handle.apply_circuit(q.gates, opts)
+        handle.apply_circuit(q.gates, topts)
+        gpu_ms["large" if q.n >= large_qubits else "small"] += handle.stats()["kernel_ms"]
         handle.probabilities(p)
         r.probs = p.cpu().numpy() if keep_outputs else None
         r.finish = time.perf_counter() - t0
@@ -240,7 +249,11 @@ def run_serial(requests, opts=None, time_scale=1.0, keep_outputs=True):
     if handle is not None:
         handle.close()
     wall = max(r.finish for r in results) - min(r.arrival for r in results)
-    return results, summarize(results, wall)
+    st = summarize(results, wall)
+    st["tile_pass_gpu_s"] = {k: round(v / 1e3, 3) for k, v in gpu_ms.items()}
+    if gpu_ms["large"] > 0:
+        st["throughput_bound_small_hidden"] = round(len(results) / (gpu_ms["large"] / 1e3), 3)
+    return results, st
 
 
 def mean_service_time(requests, opts=None):
