@@ -182,32 +182,27 @@ __device__ __forceinline__ void op_dense(Cx<R>* sm, int m, const DevOp& op, cons
 // non-local qubit, from the tile's base index); the bits below log2 of the
 // CTA size come from the thread id and are gathered once per op.
 struct DiagIndex {
-    int idx_t;      // table-index bits fixed for this thread
-    int hp[5], hb[5];  // high tile positions (relative to the CTA size) and their table bits
-    int nh;
-    int sw_t;       // swizzle of the thread's part of i
+    int idx_t;  // table-index bits fixed for this thread
+    int hp;     // 5 bits per table bit j: its tile position relative to the CTA size, or 31
+    int sw_t;   // swizzle of the thread's part of i
 };
 
 template <typename SwzT, int LT = 8>  // LT = log2 of the CTA size
 __device__ __forceinline__ DiagIndex diag_index(const DevOp& op, uint64_t tile_base) {
     DiagIndex d;
     d.idx_t = 0;
-    d.nh = 0;
+    d.hp = 0;
     const int t = threadIdx.x;
 #pragma unroll
     for (int j = 0; j < 5; j++) {
-        d.hp[j] = 0;
-        d.hb[j] = 0;
+        int h = 31;  // (it >> 31) & 1 = 0: the bit is not taken from it
         if (j < op.k) {
             const int p = op.pos[j];
             if (p < 0) d.idx_t |= (int)((tile_base >> op.qbit[j]) & 1) << j;
             else if (p < LT) d.idx_t |= ((t >> p) & 1) << j;
-            else {
-                d.hp[d.nh] = p - LT;
-                d.hb[d.nh] = j;
-                d.nh++;
-            }
+            else h = p - LT;
         }
+        d.hp |= h << (5 * j);
     }
     d.sw_t = swz<SwzT>(t);
     return d;
@@ -217,30 +212,56 @@ template <typename SwzT, int LT = 8>
 __device__ __forceinline__ void diag_at(const DiagIndex& d, int it, int& idx, int& sidx) {
     idx = d.idx_t;
 #pragma unroll
-    for (int j = 0; j < 5; j++)
-        if (j < d.nh) idx |= ((it >> d.hp[j]) & 1) << d.hb[j];
+    for (int j = 0; j < 5; j++) idx |= ((it >> ((d.hp >> (5 * j)) & 31)) & 1) << j;
     sidx = d.sw_t ^ swz<SwzT>(it << LT);
+}
+
+// Applies a <- f(u, a) to every amplitude of the tile (u its phase-table
+// entry), U amplitudes of a thread at a time: their loads are all issued
+// before their stores, so the U table and tile reads overlap.
+template <int U, int LT, typename SwzT, typename T, typename E, typename F>
+__device__ __forceinline__ void diag_sweep(T* sm, int m, const DiagIndex& d, const E* M, F f) {
+    const int N = 1 << m;
+    if (N >= (1 << LT)) {
+        const int iters = N >> LT;
+        int it = 0;
+        for (; it + U <= iters; it += U) {
+            int idx[U], si[U];
+            E u[U];
+            T a[U];
+#pragma unroll
+            for (int q = 0; q < U; q++) diag_at<SwzT, LT>(d, it + q, idx[q], si[q]);
+#pragma unroll
+            for (int q = 0; q < U; q++) {
+                u[q] = M[idx[q]];
+                a[q] = sm[si[q]];
+            }
+#pragma unroll
+            for (int q = 0; q < U; q++) sm[si[q]] = f(u[q], a[q]);
+        }
+        for (; it < iters; it++) {
+            int idx, si;
+            diag_at<SwzT, LT>(d, it, idx, si);
+            sm[si] = f(M[idx], sm[si]);
+        }
+    } else if ((int)threadIdx.x < N) {  // a tile smaller than the CTA: threads past N idle
+        int idx, si;
+        diag_at<SwzT, LT>(d, 0, idx, si);
+        sm[si] = f(M[idx], sm[si]);
+    }
 }
 
 template <typename R, int LT = 8>  // LT = log2 of the CTA size
 __device__ __forceinline__ void op_diag(Cx<R>* sm, int m, const DevOp& op, const Cx<R>* __restrict__ M,
                                         uint64_t tile_base) {
     const DiagIndex d = diag_index<R, LT>(op, tile_base);
-    const int N = 1 << m;
-    const int iters = (N + (1 << LT) - 1) >> LT;  // tiles smaller than the CTA: threads past N idle
-    const bool sign_only = op.flags & OPF_SIGN_ONLY;
-    for (int it = 0; it < iters; it++) {
-        if ((int)threadIdx.x + (it << LT) >= N) break;
-        int idx, si;
-        diag_at<R, LT>(d, it, idx, si);
-        const Cx<R> u = M[idx];
-        const Cx<R> a = sm[si];
-        if (sign_only) {
-            if (u.re < R(0)) sm[si] = Cx<R>{-a.re, -a.im};
-        } else {
-            sm[si] = Cx<R>{fmaT(u.re, a.re, -u.im * a.im), fmaT(u.re, a.im, u.im * a.re)};
-        }
-    }
+    constexpr int U = sizeof(R) == 4 ? 4 : 2;
+    if (op.flags & OPF_SIGN_ONLY)
+        diag_sweep<U, LT, R>(sm, m, d, M, [](Cx<R> u, Cx<R> a) { return u.re < R(0) ? Cx<R>{-a.re, -a.im} : a; });
+    else
+        diag_sweep<U, LT, R>(sm, m, d, M, [](Cx<R> u, Cx<R> a) {
+            return Cx<R>{fmaT(u.re, a.re, -u.im * a.im), fmaT(u.re, a.im, u.im * a.re)};
+        });
 }
 
 // ---------------------------------------------------------------------------
@@ -485,18 +506,12 @@ __device__ __forceinline__ void op_dense_df(DF4* sm, int m, const DevOp& op, con
 __device__ __forceinline__ void op_diag_df(DF4* sm, int m, const DevOp& op, const DF4* __restrict__ M,
                                            uint64_t tile_base) {
     const DiagIndex d = diag_index<double>(op, tile_base);
-    const int N = 1 << m;
-    const int iters = (N + 255) >> 8;  // tiles smaller than the CTA: threads past N idle
-    const bool sign_only = op.flags & OPF_SIGN_ONLY;
-    for (int it = 0; it < iters; it++) {
-        if ((int)threadIdx.x + (it << 8) >= N) break;
-        int idx, si;
-        diag_at<double>(d, it, idx, si);
-        const DF4 u = M[idx];
-        const DF4 a = sm[si];
-        if (sign_only) {
-            if (u.rh < 0.f) sm[si] = DF4{-a.rh, -a.rl, -a.ih, -a.il};
-        } else {
+    if (op.flags & OPF_SIGN_ONLY) {
+        diag_sweep<2, 8, double>(sm, m, d, M, [](DF4 u, DF4 a) {
+            return u.rh < 0.f ? DF4{-a.rh, -a.rl, -a.ih, -a.il} : a;
+        });
+    } else {
+        diag_sweep<2, 8, double>(sm, m, d, M, [](DF4 u, DF4 a) {
             float rh, rl, ih, il;
             df_mul(rh, rl, u.rh, u.rl, a.rh, a.rl);
             df_mac(rh, rl, -u.ih, -u.il, a.ih, a.il);
@@ -504,8 +519,8 @@ __device__ __forceinline__ void op_diag_df(DF4* sm, int m, const DevOp& op, cons
             df_mac(ih, il, u.ih, u.il, a.rh, a.rl);
             df_norm(rh, rl);
             df_norm(ih, il);
-            sm[si] = DF4{rh, rl, ih, il};
-        }
+            return DF4{rh, rl, ih, il};
+        });
     }
 }
 
@@ -723,21 +738,13 @@ template <int LT = 8>  // log2 of the CTA size
 __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const Q2* __restrict__ M,
                                            uint64_t tile_base) {
     const DiagIndex d = diag_index<double, LT>(op, tile_base);
-    const int N = 1 << m;
-    const int iters = (N + (1 << LT) - 1) >> LT;
-    const bool sign_only = op.flags & OPF_SIGN_ONLY;
-    for (int it = 0; it < iters; it++) {
-        if ((int)threadIdx.x + (it << LT) >= N) break;
-        int idx, si;
-        diag_at<double, LT>(d, it, idx, si);
-        const Q2 u = M[idx];
-        const Q2 a = sm[si];
-        if (sign_only) {
-            if (u.re < 0) sm[si] = Q2{-a.re, -a.im};
-        } else {
-            sm[si] = Q2{qmul(u.re, a.re) - qmul(u.im, a.im), qmul(u.re, a.im) + qmul(u.im, a.re)};
-        }
-    }
+    // one amplitude a thread at a time: two push the tcgen05 kernel past its 128 registers
+    if (op.flags & OPF_SIGN_ONLY)
+        diag_sweep<1, LT, double>(sm, m, d, M, [](Q2 u, Q2 a) { return u.re < 0 ? Q2{-a.re, -a.im} : a; });
+    else
+        diag_sweep<1, LT, double>(sm, m, d, M, [](Q2 u, Q2 a) {
+            return Q2{qmul(u.re, a.re) - qmul(u.im, a.im), qmul(u.re, a.im) + qmul(u.im, a.re)};
+        });
 }
 
 // ---------------------------------------------------------------------------
@@ -1396,6 +1403,9 @@ __host__ __device__ constexpr int tile_threads(int mode) {
 
 template <int MODE>
 struct TileTraits;
+// Bytes of one diagonal entry in a mode's coefficient array: Q56 / Q62 pairs
+// (tensor-core complex128), double-float quadruples, complex128 or complex64.
+__host__ __device__ constexpr int diag_entry_bytes(int mode) { return mode == MODE_F32 || mode == MODE_T32 ? 8 : 16; }
 template <>
 struct TileTraits<MODE_F32> {
     using Store = Cx<float>;
@@ -1551,6 +1561,7 @@ __global__ void __launch_bounds__(tile_threads(MODE), MODE == MODE_TC ? 2 : 1)
     __shared__ uint32_t t05_tmem;
     constexpr int kOpCache = 48;  // the pass's op descriptors, read once per pass
     __shared__ DevOp s_ops[kOpCache];
+    __shared__ __align__(16) uint4 s_diag[32];  // the current diagonal op's entries (at most 32 x 16 bytes)
     __shared__ __align__(16) int s_tab[uses_tmem(MODE) ? kOpCache * t05::kTabInts : 4];
     // complex128 digits: the constant B slice of the accumulator preload (7R x 16 fp16, K-major
     // core matrices: 8-row groups 256 bytes apart, the two 8-element K halves 128 bytes apart)
@@ -1754,11 +1765,23 @@ __global__ void __launch_bounds__(tile_threads(MODE), MODE == MODE_TC ? 2 : 1)
         const int n_ops = P.n_ops, op0 = P.op0;
         for (int o = 0; o < n_ops; o++) {
             const DevOp op = n_ops <= kOpCache ? s_ops[o] : ops[op0 + o];
+            // a diagonal op's 2^k entries (at most 32) are staged in shared
+            // memory by every thread, so each amplitude reads its phase there
+            // (the previous op ended with a barrier)
+            const typename Tr::Coef* opc = coef + op.coeff;
+            if (op.kind == OP_DIAG) {
+                constexpr int kEB = diag_entry_bytes(MODE);
+                const unsigned* src = reinterpret_cast<const unsigned*>(opc);
+                unsigned* dst = reinterpret_cast<unsigned*>(s_diag);
+                for (int i = threadIdx.x; i < (kEB / 4) << op.k; i += blockDim.x) dst[i] = src[i];
+                __syncthreads();
+                opc = reinterpret_cast<const typename Tr::Coef*>(s_diag);
+            }
             if constexpr (MODE == MODE_T05) {
                 if (op.kind == OP_PERM)
                     apply_perm<Q2, double>(sm, m, op, coef + op.coeff);
                 else if (op.kind == OP_DIAG)
-                    op_diag_tc<t05::kLogThreads>(sm, m, op, reinterpret_cast<const Q2*>(coef + op.coeff), base);
+                    op_diag_tc<t05::kLogThreads>(sm, m, op, reinterpret_cast<const Q2*>(opc), base);
                 else {
                     const int* tab = n_ops <= kOpCache ? s_tab + o * t05::kTabInts : nullptr;
                     if (op.k <= 3) t05::op_dense<3>(sm, m, op, coef + op.coeff, cx, tab);
@@ -1770,8 +1793,7 @@ __global__ void __launch_bounds__(tile_threads(MODE), MODE == MODE_TC ? 2 : 1)
                     apply_perm<Cx<float>, float>(sm, m, op, coef + op.coeff);
                 } else if (op.kind == OP_DIAG) {
                     if (threadIdx.x < t05::kThreads)  // the issuing warp sits out the 512-thread sweep
-                        op_diag<float, t05::kLogThreads>(sm, m, op,
-                                                         reinterpret_cast<const Cx<float>*>(coef + op.coeff), base);
+                        op_diag<float, t05::kLogThreads>(sm, m, op, reinterpret_cast<const Cx<float>*>(opc), base);
                 }
                 else {
                     const int* tab = n_ops <= kOpCache ? s_tab + o * t05::kTabInts : nullptr;
@@ -1781,7 +1803,7 @@ __global__ void __launch_bounds__(tile_threads(MODE), MODE == MODE_TC ? 2 : 1)
                 }
                 if (cx.failed) break;
             } else {
-                apply_op<MODE, KMAX>(sm, m, op, coef + op.coeff, base);
+                apply_op<MODE, KMAX>(sm, m, op, opc, base);
             }
             __syncthreads();
         }
