@@ -743,7 +743,12 @@ __device__ __forceinline__ void op_diag_tc(Q2* sm, int m, const DevOp& op, const
         diag_sweep<1, LT, double>(sm, m, d, M, [](Q2 u, Q2 a) { return u.re < 0 ? Q2{-a.re, -a.im} : a; });
     else
         diag_sweep<1, LT, double>(sm, m, d, M, [](Q2 u, Q2 a) {
-            return Q2{qmul(u.re, a.re) - qmul(u.im, a.im), qmul(u.re, a.im) + qmul(u.im, a.re)};
+            // three products instead of four (Gauss): k1 = c (x + y), k2 = x (d - c),
+            // k3 = y (c + d) for u = c + i d, a = x + i y; re = k1 - k3, im = k1 + k2,
+            // each off by less than two units after the floors, as the four-product
+            // form is.  |x + y| <= sqrt(2) |a| and |d -/+ c| <= sqrt(2) 2^62 stay in range.
+            const long long k1 = qmul(u.re, a.re + a.im);
+            return Q2{k1 - qmul(a.im, u.re + u.im), k1 + qmul(a.re, u.im - u.re)};
         });
 }
 
